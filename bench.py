@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Poisson solves/s to relative residual 1e-6 with the DDM-GNN preconditioner on one B300,
+against the GPU DDM-LU preconditioner on the same partition; p50/p99 latency.
+
+A step is one whole solve of the synthetic workload (default ``star100k``: a
+random star-shaped 12-gon, ~100k nodes, K = round(n_free/1000) subdomains,
+2-layer overlap, DSS kbar = 30, d = 10, FP32 GNN, FCG(10) in FP64 to 1e-6):
+assembly, decomposition (partition, overlap, local graphs, coarse matrix and
+its inverse), preconditioner set-up and the Krylov loop.  ``value`` times steps
+whose mesh already sits in HBM; ``e2e`` times the same through the C ABI from
+host buffers (mesh upload and solution download inside the timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs an independent replica (the solver does not
+shard across GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s to rel.res 1e-6, GNN vs LU-Schwarz on 1 B300; p50/p99 latency"
+KBAR, D, ALPHA = 30, 10, 1e-3
+WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="star100k")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=1500)
+    ap.add_argument("--m", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- workload
+def load_weights(synth):
+    if os.path.exists(WEIGHTS):
+        return np.load(WEIGHTS).astype(np.float32), "trained"
+    return synth.dss_weights(KBAR, D, 0), "xavier"
+
+
+def dss_flops(ddg, p) -> float:
+    """Algorithmic FP32 FLOPs of one GNN launch in factorised form (multiply-add = 2)."""
+    loc_ptr, n_int, _, nbr_ptr, nbr = ddg.ddg_graph_download(p)
+    K = n_int.shape[0]
+    nodes = int(loc_ptr[-1])
+    unknowns = int(n_int.sum())
+    msgs = 0
+    eo = 0
+    for i in range(K):
+        ptr = nbr_ptr[loc_ptr[i] + i: loc_ptr[i + 1] + i + 1]
+        nl = loc_ptr[i + 1] - loc_ptr[i]
+        lst = nbr[eo: eo + ptr[-1]]
+        eo += ptr[-1]
+        k = n_int[i]
+        ends = ptr[1:]
+        inner_deg = ends[:k] - ptr[:k]
+        msgs += int(inner_deg.sum())                       # in-messages of unknowns
+        msgs += int(np.sum(lst[:ptr[k]] < k))              # out-messages of unknowns
+        msgs += int(ptr[nl] - ptr[k])                      # out-messages of halo nodes
+    node_flops = 2 * (4 * D * D + 2 * D * D + (3 * D + 1) * D + D * D + D) + 6 * D
+    msg_flops = 2 * 3 * D + 3 * D
+    dec_flops = 2 * (D * D + D) + 2 * D
+    return float(KBAR * (nodes * node_flops + msgs * msg_flops) + unknowns * dec_flops), nodes, msgs
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_2402_08296_b300 as ddg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = synth.workload(a.workload, a.seed + rank)
+    W, wkind = load_weights(synth)
+    ctx = ddg.ddg_create(local_rank)
+    stream = torch.cuda.ExternalStream(ddg.ddg_get_stream(ctx), device=f"cuda:{local_rank}")
+    model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, W)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    p = ddg.ddg_mesh_upload(ctx, w.mesh.xy, w.mesh.tri)
+
+    def step(kind, problem, want_x=False):
+        ddg.ddg_assemble_poly(problem, w.coeffs)
+        ddg.ddg_partition(problem, w.K, w.overlap)
+        ddg.ddg_setup_precond(problem, kind, model if kind == ddg.DDG_DDM_GNN else None, ddg.DDG_COARSE)
+        return ddg.ddg_fcg_solve(problem, a.tol, a.max_iter, a.m, want_x=want_x)
+
+    def timed(fn, n):
+        """n steps, each bracketed by events on the library stream; L2 flushed between steps."""
+        times, reps, launches = [], [], 0
+        for _ in range(n):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = ddg.ddg_launch_count()
+            e0.record(stream)
+            rep = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            launches += ddg.ddg_launch_count() - l0
+            times.append(e0.elapsed_time(e1))
+            reps.append(rep)
+        return np.array(times), reps, launches
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (both kinds), then the timed regions
+    for _ in range(a.warmup):
+        step(ddg.DDG_DDM_GNN, p)
+        step(ddg.DDG_DDM_LU, p)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    barrier()
+    t_gnn, r_gnn, launches = timed(lambda: step(ddg.DDG_DDM_GNN, p)[0], a.steps)
+    barrier()
+    t_lu, r_lu, _ = timed(lambda: step(ddg.DDG_DDM_LU, p)[0], a.steps)
+    barrier()
+
+    def e2e_step():
+        q = ddg.ddg_mesh_upload(ctx, w.mesh.xy, w.mesh.tri)
+        try:
+            rep, x = step(ddg.DDG_DDM_GNN, q, want_x=True)
+        finally:
+            ddg.ddg_problem_destroy(q)
+        return rep, x
+
+    t0 = time.perf_counter()
+    t_e2e, r_e2e, _ = timed(lambda: e2e_step()[0], a.steps)
+    wall_e2e = time.perf_counter() - t0
+    barrier()
+    clk = clocks.stop()
+
+    # solver-only timing of the dominant kernel inside the timed GNN steps
+    local_ms = sum(r["local_ms"] for r in r_gnn)
+    local_launches = sum(r["local_launches"] for r in r_gnn)
+    ddg.ddg_assemble_poly(p, w.coeffs)
+    ddg.ddg_partition(p, w.K, w.overlap)
+    flops, nodes, msgs = dss_flops(ddg, p)
+    info = ddg.ddg_problem_info(p)
+
+    tot_gnn = max_over_ranks(float(t_gnn.sum()) / 1e3)
+    tot_lu = max_over_ranks(float(t_lu.sum()) / 1e3)
+    tot_e2e = max_over_ranks(float(t_e2e.sum()) / 1e3)
+    if rank != 0:
+        return None
+    avg_launch_s = (local_ms / max(local_launches, 1)) / 1e3
+    achieved = flops / avg_launch_s / 1e12 if local_launches else None
+    sm_max = 2032.0
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+    iters = [r["iterations"] for r in r_gnn]
+    conv = all(r["status"] == 0 for r in r_gnn)
+    out = {
+        "metric": METRIC,
+        "value": a.steps * world / tot_gnn,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": float(t_gnn.mean()),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 GNN / f64 Krylov",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "n_nodes": info["n_nodes"], "n_free": info["n_free"], "K": info["K"],
+                   "overlap": w.overlap, "kbar": KBAR, "d": D, "alpha": ALPHA, "fcg_m": a.m, "tol": a.tol,
+                   "weights": wkind, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "converged": conv,
+        "gnn": {"iterations": iters, "true_rel_residual": [r["true_rel_residual"] for r in r_gnn],
+                "p50_ms": float(np.percentile(t_gnn, 50)), "p99_ms": float(np.percentile(t_gnn, 99)),
+                "solve_ms": [r["solve_ms"] for r in r_gnn], "precond_ms": [r["precond_ms"] for r in r_gnn]},
+        "lu": {"value": a.steps * world / tot_lu, "unit": "solves/s",
+               "iterations": [r["iterations"] for r in r_lu],
+               "true_rel_residual": [r["true_rel_residual"] for r in r_lu],
+               "p50_ms": float(np.percentile(t_lu, 50)), "p99_ms": float(np.percentile(t_lu, 99)),
+               "solve_ms": [r["solve_ms"] for r in r_lu]},
+        "e2e": {"value": a.steps * world / tot_e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": int(w.mesh.xy.nbytes + w.mesh.t * 12 + 72),
+                "d2h_bytes_per_step": int(w.mesh.n * 8 + 64), "wall_s": wall_e2e,
+                "p50_ms": float(np.percentile(t_e2e, 50)), "p99_ms": float(np.percentile(t_e2e, 99))},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_dss (batched DSS inference)", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                     "flops_per_launch": flops, "nodes": nodes, "messages": msgs,
+                     "avg_launch_ms": avg_launch_s * 1e3,
+                     "peak_note": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (unit counts and max clock)"},
+        "clocks": clk,
+    }
+    return out
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(a, budget_s: float):
+    """Time the oracle on a bounded sample of the workload and scale it to one solve.
+
+    Sample: assembly + decomposition of the full mesh, then DSS inferences on
+    as many subdomains as fit the budget, scaled to all K subdomains and to
+    the iteration count given (one preconditioner application per iteration).
+    """
+    import synth
+    from oracle import ddm, dss, fem, partition as pt
+
+    w = synth.workload(a.workload, a.seed)
+    W, _ = load_weights(synth)
+    t0 = time.perf_counter()
+    P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
+    Dd = pt.decompose(P, w.K, w.overlap)
+    adj = pt.mesh_adjacency(P.n, P.tri)
+    hbar = pt.mean_edge_length(P.xy, P.tri)
+    t_setup = time.perf_counter() - t0
+    r = P.b
+    done, t_dss = 0, 0.0
+    for i, S in enumerate(Dd.sets):
+        t1 = time.perf_counter()
+        g = pt.local_graph(P, S, adj)
+        s = np.linalg.norm(r[S])
+        dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / s, W, KBAR, D, ALPHA, hbar)
+        t_dss += time.perf_counter() - t1
+        done += 1
+        if t_setup + t_dss > budget_s:
+            break
+    per_apply = t_dss / done * w.K
+    return {"t_setup_s": t_setup, "per_precond_s": per_apply, "subdomains_sampled": done, "K": w.K,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return None
+    times = []
+    samp = None
+    for _ in range(a.warmup + a.steps):
+        samp = oracle_sample(a, a.cpu_seconds / max(1, a.warmup + a.steps))
+        times.append(samp["t_setup_s"] + a.max_iter_ref * samp["per_precond_s"])
+    t = np.array(times[a.warmup:])
+    v = 1.0 / float(t.mean())
+    return {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": float(t.mean() * 1e3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": a.workload, "kbar": KBAR, "d": D, "tol": a.tol},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": samp["cores"], "kind": "oracle",
+                             "sample": f"assembly + decomposition + DSS on {samp['subdomains_sampled']} of "
+                                       f"{samp['K']} subdomains, scaled to {a.max_iter_ref} preconditioner "
+                                       f"applications"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = args_parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    a.max_iter_ref = 50
+    if a.impl == "reference":
+        out = run_reference(a, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(a, rank, world, local_rank)
+    if out is None:
+        return
+    if world == 1 and not a.no_cpu_baseline:
+        its = int(np.median(out["gnn"]["iterations"]))
+        s = oracle_sample(a, a.cpu_seconds)
+        t = s["t_setup_s"] + its * s["per_precond_s"]
+        out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": s["cores"], "kind": "oracle",
+                               "sample": f"assembly + decomposition + FP64 DSS on {s['subdomains_sampled']} of "
+                                         f"{s['K']} subdomains, scaled to {its} preconditioner applications "
+                                         f"(the GPU's iteration count)"}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * ddg.h - C ABI of the DDM-GNN solver library (libddg.so).
+ *
+ * The library solves the P1 finite-element Poisson-Dirichlet problem
+ * -Lap(u) = f in Omega, u = g on the boundary (Section II, Eqs. 1-2) with
+ * flexible conjugate gradients preconditioned by the paper's two-level
+ * additive Schwarz method, whose local solves are either exact (DDM-LU,
+ * Eq. 7) or one inference of a Deep Statistical Solver GNN (DDM-GNN,
+ * Section III-A, Eqs. 13-16; architecture Section III-B, Eqs. 18-22).
+ * Everything after the upload runs in the library's CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Every call returns an int32_t status (DDG_OK = 0 or a negative code).
+ *    No call aborts, throws or traps; after a failure ddg_last_error()
+ *    returns a message for the calling thread.
+ *  - Handles are opaque and owned by the caller, who frees them with the
+ *    matching *_destroy call.  A problem or model must be destroyed before
+ *    its context.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Host arrays passed out are written, never kept.
+ *  - Device pointers (ddg_precondition, ddg_apply_A, ddg_local_corrections)
+ *    are borrowed: they must live on the context's device and are used in
+ *    stream order on the stream given (NULL = the context's own stream).
+ *  - Indices are int32, zero-based.  "free" nodes are the mesh nodes that are
+ *    not Dirichlet nodes, numbered in ascending mesh order.
+ *  - A context and everything created from it is not thread-safe.
+ */
+#ifndef DDG_H
+#define DDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddg_ctx ddg_ctx;
+typedef struct ddg_problem ddg_problem;
+typedef struct ddg_model ddg_model;
+typedef void *ddg_stream; /* a cudaStream_t */
+
+enum ddg_status {
+    DDG_OK = 0,
+    DDG_INVALID_ARG = -1,   /* bad size, NULL pointer, call out of order */
+    DDG_OOM = -2,           /* device allocation failed or HBM budget exceeded */
+    DDG_CUDA_ERROR = -3,    /* a CUDA runtime call failed */
+    DDG_NOT_CONVERGED = -4, /* max_iter reached */
+    DDG_BREAKDOWN = -5,     /* p.q <= 0 or a non-finite scalar in the Krylov loop */
+    DDG_BAD_MESH = -9,      /* degenerate or inverted triangle, or a node of too high degree */
+    DDG_TOO_LARGE = -10     /* a subdomain or node list beyond a kernel's on-chip capacity */
+};
+
+enum ddg_precond_kind { DDG_NONE = 0, DDG_DDM_LU = 1, DDG_DDM_GNN = 2 };
+
+enum ddg_precond_flags {
+    DDG_COARSE = 1u,      /* add the Nicolaides coarse correction (two-level, Eq. 7) */
+    DDG_POU_PROLONG = 2u  /* glue local corrections with partition-of-unity weights instead of R_i^T */
+};
+
+typedef struct ddg_solve_report {
+    int32_t status;            /* DDG_OK, DDG_NOT_CONVERGED or DDG_BREAKDOWN */
+    int32_t iterations;        /* FCG iterations taken */
+    double rel_residual;       /* recursive |r| / |b| at exit */
+    double true_rel_residual;  /* |b - A x| / |b| recomputed at exit (FP64) */
+    double solve_ms;           /* device time of the Krylov loop (CUDA events on the solve stream) */
+    double precond_ms;         /* device time of all preconditioner applications */
+    double local_ms;           /* device time of the local-solve kernel alone (GNN or band solves) */
+    int32_t local_launches;    /* launches of the local-solve kernel inside the loop */
+    int32_t launches;          /* all kernel launches of the library inside the loop */
+} ddg_solve_report;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context's objects may hold (0 = no cap).  Errors:
+ * DDG_INVALID_ARG (no such device), DDG_CUDA_ERROR. */
+int32_t ddg_create(int32_t device, size_t hbm_budget_bytes, ddg_ctx **out);
+int32_t ddg_destroy(ddg_ctx *ctx);
+/* Message of the calling thread's last failure (empty string if none). */
+const char *ddg_last_error(void);
+/* Device memory currently held by the context's objects, in bytes. */
+int32_t ddg_memory_in_use(ddg_ctx *ctx, size_t *bytes);
+/* The context's own CUDA stream (a cudaStream_t), on which every call
+ * without an explicit stream runs; lets a caller record events around calls. */
+int32_t ddg_get_stream(ddg_ctx *ctx, ddg_stream *out);
+/* Number of kernel launches the library has issued in this process so far. */
+int32_t ddg_launch_count(uint64_t *out);
+
+/* ---- mesh and assembly (Section II, Eqs. 1-2) ------------------------ */
+
+/* Upload a triangle mesh: xy[2*n_nodes] FP64 coordinates (x0, y0, x1, ...),
+ * tri[3*n_tri] vertex ids, counter-clockwise.  dirichlet[n_nodes] marks the
+ * Dirichlet nodes (nonzero = Dirichlet); NULL selects the endpoints of the
+ * boundary edges (edges in exactly one triangle).  The device builds the node
+ * adjacency, checks every triangle's orientation and the mean edge length
+ * h_bar.  Errors: DDG_INVALID_ARG, DDG_BAD_MESH (area <= 0, a node in more
+ * than 32 triangles or with more than 32 neighbours), DDG_OOM. */
+int32_t ddg_mesh_upload(ddg_ctx *ctx, int32_t n_nodes, const double *xy, int32_t n_tri,
+                        const int32_t *tri, const uint8_t *dirichlet, ddg_problem **out);
+int32_t ddg_problem_destroy(ddg_problem *p);
+
+/* Assemble A_ff and b_f - A_fD g_D for the paper's data family (Section IV-A,
+ * Eqs. 24-25): f = r1 (x-1)^2 + r2 y^2 + r3 and g = r4 x^2 + r5 y^2 + r6 xy +
+ * r7 x + r8 y + r9, r = r[0..8].  The load is integrated exactly through f's
+ * P2 interpolant.  Any earlier partition or preconditioner is dropped. */
+int32_t ddg_assemble_poly(ddg_problem *p, const double r[9]);
+/* The same with nodal f[n_nodes] (consistent P1 mass matrix) and nodal
+ * g[n_nodes] (used at the Dirichlet nodes). */
+int32_t ddg_assemble_nodal(ddg_problem *p, const double *f, const double *g);
+
+/* Sizes: info[0] n_nodes, [1] n_tri, [2] n_free, [3] nnz of A_ff, [4] K,
+ * [5] sum of subdomain sizes, [6] sum of local graph sizes (with halo),
+ * [7] sum of local graph edges, [8] largest local graph, [9] h_bar as the
+ * bit pattern of an FP64 value.  Unknown entries are -1. */
+int32_t ddg_problem_info(ddg_problem *p, int64_t info[10]);
+
+/* Download the assembled free-free CSR (rowptr[n_free+1], col[nnz], val[nnz])
+ * and the right-hand side b[n_free].  Any output pointer may be NULL. */
+int32_t ddg_matrix_download(ddg_problem *p, int32_t *rowptr, int32_t *col, double *val, double *b);
+
+/* ---- decomposition (Section II-A; Section IV-A) ------------------------ */
+
+/* Split the free nodes into K parts by recursive coordinate bisection (or
+ * take part_or_NULL[n_free], values in [0, K)), grow each part by
+ * overlap_layers adjacency layers of the A_ff graph, and build the
+ * partition-of-unity weights 1/multiplicity, the local DSS graphs and the
+ * coarse matrix A_0 = Z^T A Z.  Errors: DDG_INVALID_ARG, DDG_TOO_LARGE (a
+ * node in more than 32 subdomains), DDG_OOM. */
+int32_t ddg_partition(ddg_problem *p, int32_t K, int32_t overlap_layers, const int32_t *part_or_null);
+
+/* Download part[n_free], sub_ptr[K+1], sub_idx[sum k_i] (ascending free ids
+ * of every subdomain) and mult[n_free].  NULL outputs are skipped. */
+int32_t ddg_partition_download(ddg_problem *p, int32_t *part, int32_t *sub_ptr, int32_t *sub_idx, int32_t *mult);
+
+/* Download the local graphs: loc_ptr[K+1] offsets of every graph's nodes,
+ * n_int[K], loc_node[sum n_loc] mesh ids (unknowns ascending, then halo
+ * ascending), nbr_ptr[sum n_loc + K] per-graph CSR offsets (graph i's slice
+ * starts at loc_ptr[i] + i), nbr[sum edges] local neighbour ids: every mesh
+ * neighbour for an unknown, the unknown neighbours for a halo node.
+ * NULL outputs are skipped. */
+int32_t ddg_graph_download(ddg_problem *p, int32_t *loc_ptr, int32_t *n_int, int32_t *loc_node,
+                           int32_t *nbr_ptr, int32_t *nbr);
+
+/* Download A_0 (K*K, row-major) and its inverse as the setup computed it. */
+int32_t ddg_coarse_download(ddg_problem *p, double *A0, double *A0_inv);
+
+/* ---- DSS model (Section III-B; Table 2) -------------------------------- */
+
+/* Create a model with kbar blocks of latent size d (d = 10 is compiled) and
+ * ResNet step alpha.  w (n_w = kbar * (11 d^2 + 15 d + 1) floats, layout per
+ * block row-major W[out][in]: Phi_out W1[d][2d+3] b1[d] W2[d][d] b2[d];
+ * Phi_in the same; Psi W1[d][3d+1] b1[d] W2[d][d] b2[d]; D W1[d][d] b1[d]
+ * W2[1][d] b2[1]) or NULL for Xavier-uniform matrices and zero biases drawn
+ * from SplitMix64(seed).  Errors: DDG_INVALID_ARG (n_w mismatch, d != 10). */
+int32_t ddg_model_create(ddg_ctx *ctx, int32_t kbar, int32_t d, float alpha, const float *w, size_t n_w,
+                         uint64_t seed, ddg_model **out);
+int32_t ddg_model_destroy(ddg_model *m);
+int32_t ddg_model_get_weights(ddg_model *m, float *w, size_t n_w);
+
+/* ---- preconditioner and solver --------------------------------------- */
+
+/* Build the preconditioner of the given kind on the current partition:
+ * DDG_DDM_LU factorises every R_i A R_i^T (banded FP64 Cholesky);
+ * DDG_DDM_GNN uses `model` (kept by reference; it must outlive its use).
+ * flags: DDG_COARSE, DDG_POU_PROLONG.  Errors: DDG_INVALID_ARG (no
+ * partition, missing model), DDG_TOO_LARGE (a local graph beyond the GNN
+ * kernel's 2048 nodes), DDG_OOM. */
+int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, uint32_t flags);
+
+/* z = M^-1 r for device vectors r_dev, z_dev of n_free FP64 (Eqs. 13-16 for
+ * DDM-GNN, Eq. 7 for DDM-LU, z = r for DDG_NONE). */
+int32_t ddg_precondition(ddg_problem *p, const double *r_dev, double *z_dev, ddg_stream stream);
+
+/* The local corrections alone: s_dev[K] = |R_i r| and corr_dev[sum k_i] (in
+ * sub_idx order) = |R_i r| r~_i for DDM-GNN or (R_i A R_i^T)^-1 R_i r for DDM-LU. */
+int32_t ddg_local_corrections(ddg_problem *p, const double *r_dev, double *corr_dev, double *s_dev,
+                              ddg_stream stream);
+
+/* y = A_ff x for device vectors of n_free FP64. */
+int32_t ddg_apply_A(ddg_problem *p, const double *x_dev, double *y_dev, ddg_stream stream);
+
+/* Solve A_ff x = b_f by flexible CG (truncation m_trunc >= 1; m_trunc = 1
+ * reproduces PCG for a fixed SPD preconditioner) from x0 (host, n_free, or
+ * NULL = 0) until |r| / |b| < rtol or max_iter iterations.  x_host[n_nodes]
+ * receives the full nodal solution (g on Dirichlet nodes).  Returns the
+ * report's status. */
+int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,
+                      double *x_host, ddg_solve_report *report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDG_H */

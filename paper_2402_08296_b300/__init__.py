@@ -1,0 +1,303 @@
+"""Python binding of libddg, the B300 DDM-GNN Poisson solver (C ABI in include/ddg.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+The functions keep the C names; handles are opaque ``ctypes.c_void_p`` values.
+Host arrays are numpy arrays (copied by the library); device arrays are any
+object with ``data_ptr()`` (a torch CUDA tensor) or a raw integer address.
+A non-OK status raises ``DdgError`` (except ``ddg_fcg_solve``, which returns
+its report so that NOT_CONVERGED can be inspected).
+
+The shared library must exist (``paper_2402_08296_b300/libddg.so``, built by
+``python paper_2402_08296_b300/build.py`` or ``__graft_entry__.build()``);
+importing this package without it raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddg.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libddg.so is not built; run `python paper_2402_08296_b300/build.py`")
+lib = ctypes.CDLL(LIB_PATH)
+
+DDG_OK = 0
+DDG_INVALID_ARG = -1
+DDG_OOM = -2
+DDG_CUDA_ERROR = -3
+DDG_NOT_CONVERGED = -4
+DDG_BREAKDOWN = -5
+DDG_BAD_MESH = -9
+DDG_TOO_LARGE = -10
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR", -4: "NOT_CONVERGED",
+                -5: "BREAKDOWN", -9: "BAD_MESH", -10: "TOO_LARGE"}
+
+DDG_NONE, DDG_DDM_LU, DDG_DDM_GNN = 0, 1, 2
+DDG_COARSE, DDG_POU_PROLONG = 1, 2
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_sz = ctypes.c_size_t
+_f32 = ctypes.c_float
+_f64 = ctypes.c_double
+
+
+class ddg_solve_report(ctypes.Structure):
+    _fields_ = [("status", _i32), ("iterations", _i32), ("rel_residual", _f64),
+                ("true_rel_residual", _f64), ("solve_ms", _f64), ("precond_ms", _f64),
+                ("local_ms", _f64), ("local_launches", _i32), ("launches", _i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SIGS = {
+    "ddg_create": [_i32, _sz, ctypes.POINTER(_p)],
+    "ddg_destroy": [_p],
+    "ddg_memory_in_use": [_p, ctypes.POINTER(_sz)],
+    "ddg_get_stream": [_p, ctypes.POINTER(_p)],
+    "ddg_launch_count": [ctypes.POINTER(_u64)],
+    "ddg_mesh_upload": [_p, _i32, _p, _i32, _p, _p, ctypes.POINTER(_p)],
+    "ddg_problem_destroy": [_p],
+    "ddg_assemble_poly": [_p, _p],
+    "ddg_assemble_nodal": [_p, _p, _p],
+    "ddg_problem_info": [_p, _p],
+    "ddg_matrix_download": [_p, _p, _p, _p, _p],
+    "ddg_partition": [_p, _i32, _i32, _p],
+    "ddg_partition_download": [_p, _p, _p, _p, _p],
+    "ddg_graph_download": [_p, _p, _p, _p, _p, _p],
+    "ddg_coarse_download": [_p, _p, _p],
+    "ddg_model_create": [_p, _i32, _i32, _f32, _p, _sz, _u64, ctypes.POINTER(_p)],
+    "ddg_model_destroy": [_p],
+    "ddg_model_get_weights": [_p, _p, _sz],
+    "ddg_setup_precond": [_p, _i32, _p, ctypes.c_uint32],
+    "ddg_precondition": [_p, _p, _p, _p],
+    "ddg_local_corrections": [_p, _p, _p, _p, _p],
+    "ddg_apply_A": [_p, _p, _p, _p],
+    "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _i32
+lib.ddg_last_error.argtypes = []
+lib.ddg_last_error.restype = ctypes.c_char_p
+
+
+class DdgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.ddg_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status: int, where: str) -> None:
+    if status != DDG_OK:
+        raise DdgError(status, where)
+
+
+def _host(a, dtype):
+    """Contiguous numpy copy/view of ``a`` with ``dtype`` and its address."""
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(_p)
+
+
+def _dev(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return _p(x)
+    return _p(x.data_ptr())
+
+
+def _stream(stream, *tensors):
+    """The stream to launch on: the given one, else torch's current stream when torch tensors are passed."""
+    if stream is None:
+        for t in tensors:
+            if hasattr(t, "data_ptr") and hasattr(t, "device"):
+                import torch
+                return _p(torch.cuda.current_stream(t.device).cuda_stream)
+        return None
+    if isinstance(stream, int):
+        return _p(stream)
+    return _p(stream.cuda_stream)
+
+
+def ddg_last_error() -> str:
+    return lib.ddg_last_error().decode(errors="replace")
+
+
+def ddg_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = _p()
+    _check(lib.ddg_create(device, hbm_budget_bytes, ctypes.byref(h)), "ddg_create")
+    return h
+
+
+def ddg_destroy(ctx) -> None:
+    _check(lib.ddg_destroy(ctx), "ddg_destroy")
+
+
+def ddg_memory_in_use(ctx) -> int:
+    v = _sz()
+    _check(lib.ddg_memory_in_use(ctx, ctypes.byref(v)), "ddg_memory_in_use")
+    return int(v.value)
+
+
+def ddg_get_stream(ctx) -> int:
+    h = _p()
+    _check(lib.ddg_get_stream(ctx, ctypes.byref(h)), "ddg_get_stream")
+    return int(h.value or 0)
+
+
+def ddg_launch_count() -> int:
+    v = _u64()
+    _check(lib.ddg_launch_count(ctypes.byref(v)), "ddg_launch_count")
+    return int(v.value)
+
+
+def ddg_mesh_upload(ctx, xy, tri, dirichlet=None):
+    xy_a, xy_p = _host(xy, np.float64)
+    tri_a, tri_p = _host(tri, np.int32)
+    d_p = None
+    if dirichlet is not None:
+        d_a, d_p = _host(dirichlet, np.uint8)
+    h = _p()
+    _check(lib.ddg_mesh_upload(ctx, xy_a.shape[0], xy_p, tri_a.shape[0], tri_p, d_p, ctypes.byref(h)),
+           "ddg_mesh_upload")
+    return h
+
+
+def ddg_problem_destroy(p) -> None:
+    _check(lib.ddg_problem_destroy(p), "ddg_problem_destroy")
+
+
+def ddg_assemble_poly(p, r) -> None:
+    r_a, r_p = _host(r, np.float64)
+    assert r_a.shape == (9,)
+    _check(lib.ddg_assemble_poly(p, r_p), "ddg_assemble_poly")
+
+
+def ddg_assemble_nodal(p, f, g) -> None:
+    f_a, f_p = _host(f, np.float64)
+    g_a, g_p = _host(g, np.float64)
+    _check(lib.ddg_assemble_nodal(p, f_p, g_p), "ddg_assemble_nodal")
+
+
+def ddg_problem_info(p) -> dict:
+    info = np.zeros(10, dtype=np.int64)
+    _check(lib.ddg_problem_info(p, info.ctypes.data_as(_p)), "ddg_problem_info")
+    keys = ["n_nodes", "n_tri", "n_free", "nnz", "K", "sum_k", "sum_loc", "sum_edges", "max_loc"]
+    out = {k: int(v) for k, v in zip(keys, info[:9])}
+    out["hbar"] = struct.unpack("<d", struct.pack("<q", int(info[9])))[0]
+    return out
+
+
+def ddg_matrix_download(p):
+    info = ddg_problem_info(p)
+    nf, nnz = info["n_free"], info["nnz"]
+    rowptr = np.zeros(nf + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    b = np.zeros(nf, np.float64)
+    _check(lib.ddg_matrix_download(p, rowptr.ctypes.data_as(_p), col.ctypes.data_as(_p), val.ctypes.data_as(_p),
+                                   b.ctypes.data_as(_p)), "ddg_matrix_download")
+    return rowptr, col, val, b
+
+
+def ddg_partition(p, K: int, overlap_layers: int, part=None) -> None:
+    pp = None
+    if part is not None:
+        part_a, pp = _host(part, np.int32)
+    _check(lib.ddg_partition(p, K, overlap_layers, pp), "ddg_partition")
+
+
+def ddg_partition_download(p):
+    info = ddg_problem_info(p)
+    nf, K, sk = info["n_free"], info["K"], info["sum_k"]
+    part = np.zeros(nf, np.int32)
+    sub_ptr = np.zeros(K + 1, np.int32)
+    sub_idx = np.zeros(sk, np.int32)
+    mult = np.zeros(nf, np.int32)
+    _check(lib.ddg_partition_download(p, part.ctypes.data_as(_p), sub_ptr.ctypes.data_as(_p),
+                                      sub_idx.ctypes.data_as(_p), mult.ctypes.data_as(_p)), "ddg_partition_download")
+    return part, sub_ptr, sub_idx, mult
+
+
+def ddg_graph_download(p):
+    info = ddg_problem_info(p)
+    K, sl, se = info["K"], info["sum_loc"], info["sum_edges"]
+    loc_ptr = np.zeros(K + 1, np.int32)
+    n_int = np.zeros(K, np.int32)
+    loc_node = np.zeros(sl, np.int32)
+    nbr_ptr = np.zeros(sl + K, np.int32)
+    nbr = np.zeros(se, np.int32)
+    _check(lib.ddg_graph_download(p, loc_ptr.ctypes.data_as(_p), n_int.ctypes.data_as(_p), loc_node.ctypes.data_as(_p),
+                                  nbr_ptr.ctypes.data_as(_p), nbr.ctypes.data_as(_p)), "ddg_graph_download")
+    return loc_ptr, n_int, loc_node, nbr_ptr, nbr
+
+
+def ddg_coarse_download(p):
+    K = ddg_problem_info(p)["K"]
+    A0 = np.zeros((K, K))
+    A0inv = np.zeros((K, K))
+    _check(lib.ddg_coarse_download(p, A0.ctypes.data_as(_p), A0inv.ctypes.data_as(_p)), "ddg_coarse_download")
+    return A0, A0inv
+
+
+def ddg_model_create(ctx, kbar: int, d: int, alpha: float, w=None, seed: int = 0):
+    n_w = kbar * (11 * d * d + 15 * d + 1)
+    wp = None
+    if w is not None:
+        w_a, wp = _host(w, np.float32)
+        assert w_a.size == n_w
+    h = _p()
+    _check(lib.ddg_model_create(ctx, kbar, d, alpha, wp, n_w, seed, ctypes.byref(h)), "ddg_model_create")
+    return h
+
+
+def ddg_model_destroy(m) -> None:
+    _check(lib.ddg_model_destroy(m), "ddg_model_destroy")
+
+
+def ddg_model_get_weights(m, n_w: int) -> np.ndarray:
+    w = np.zeros(n_w, np.float32)
+    _check(lib.ddg_model_get_weights(m, w.ctypes.data_as(_p), n_w), "ddg_model_get_weights")
+    return w
+
+
+def ddg_setup_precond(p, kind: int, model=None, flags: int = DDG_COARSE) -> None:
+    _check(lib.ddg_setup_precond(p, kind, model, flags), "ddg_setup_precond")
+
+
+def ddg_precondition(p, r_dev, z_dev, stream=None) -> None:
+    _check(lib.ddg_precondition(p, _dev(r_dev), _dev(z_dev), _stream(stream, r_dev, z_dev)), "ddg_precondition")
+
+
+def ddg_local_corrections(p, r_dev, corr_dev, s_dev, stream=None) -> None:
+    _check(lib.ddg_local_corrections(p, _dev(r_dev), _dev(corr_dev), _dev(s_dev), _stream(stream, r_dev)),
+           "ddg_local_corrections")
+
+
+def ddg_apply_A(p, x_dev, y_dev, stream=None) -> None:
+    _check(lib.ddg_apply_A(p, _dev(x_dev), _dev(y_dev), _stream(stream, x_dev, y_dev)), "ddg_apply_A")
+
+
+def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: bool = True):
+    """Returns (report dict, x over all mesh nodes or None)."""
+    info = ddg_problem_info(p)
+    x0p = None
+    if x0 is not None:
+        x0_a, x0p = _host(x0, np.float64)
+    x = np.zeros(info["n_nodes"], np.float64) if want_x else None
+    rep = ddg_solve_report()
+    st = lib.ddg_fcg_solve(p, x0p, rtol, max_iter, m_trunc, x.ctypes.data_as(_p) if want_x else None,
+                           ctypes.byref(rep))
+    if st not in (DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN):
+        raise DdgError(st, "ddg_fcg_solve")
+    return rep.as_dict(), x

@@ -1,0 +1,218 @@
+// Internal declarations of libddg: object layouts, error plumbing, device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ddg.h"
+
+namespace ddg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+void clear_error();
+
+#define DDG_CU(call)                                                                      \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ddg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return DDG_CUDA_ERROR;                                                        \
+        }                                                                                 \
+    } while (0)
+
+#define DDG_TRY(call)                   \
+    do {                                \
+        int32_t s_ = (call);            \
+        if (s_ != DDG_OK) return s_;    \
+    } while (0)
+
+// every launch site is followed by DDG_LAUNCH_CHECK (or DDG_LAUNCHES(n) for n launches)
+void note_launches(int n);
+#define DDG_LAUNCHES(n)           \
+    do {                          \
+        ddg::note_launches(n);    \
+        DDG_CU(cudaGetLastError()); \
+    } while (0)
+#define DDG_LAUNCH_CHECK() DDG_LAUNCHES(1)
+
+// device status bits raised by bounded checks inside kernels
+enum : int {
+    ST_BAD_MESH = 1,      // non-positive triangle area, node degree over the cap
+    ST_TOO_LARGE = 2,     // list longer than a kernel's local capacity
+    ST_BAD_INPUT = 4,     // user partition value out of range
+};
+
+constexpr int MAX_NODE_TRI = 32;   // triangles around one node
+constexpr int MAX_NODE_NBR = 32;   // mesh neighbours of one node
+constexpr int MAX_MEMBERSHIP = 32; // subdomains holding one node
+constexpr int DSS_D = 10;          // latent size compiled into the GNN kernel
+constexpr int DSS_THREADS = 512;
+constexpr int DSS_MAX_NODES = 2048; // local graph nodes (unknowns + halo) per CTA
+
+// ---------------------------------------------------------------- allocation
+struct Allocs {
+    std::vector<void *> ptrs;
+    std::vector<size_t> sizes;
+};
+
+}  // namespace ddg
+
+struct ddg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+};
+
+struct ddg_model {
+    ddg_ctx *ctx = nullptr;
+    int kbar = 0, d = 0;
+    float alpha = 0.f;
+    size_t n_w = 0;
+    float *w = nullptr;       // flat weights as given (device)
+    float *packed = nullptr;  // per-block padded layout read by the GNN kernel (device)
+    size_t packed_per_block = 0;
+    ddg::Allocs allocs;
+};
+
+struct ddg_problem {
+    ddg_ctx *ctx = nullptr;
+    int *d_status = nullptr;  // device status word (bits ST_*)
+
+    // mesh (stage "mesh")
+    int n = 0, t = 0;
+    double *xy = nullptr;      // [2n]
+    int *tri = nullptr;        // [3t]
+    uint8_t *dir = nullptr;    // [n] Dirichlet flags
+    int *ntri_ptr = nullptr, *ntri_idx = nullptr;  // node -> incident triangles (ascending)
+    int *adj_ptr = nullptr, *adj_idx = nullptr;    // node -> mesh neighbours (ascending)
+    int n_edges = 0;
+    double hbar = 0.0;
+    int nf = 0;
+    int *free_id = nullptr;    // [n], -1 on Dirichlet nodes
+    int *free_node = nullptr;  // [nf]
+    double *xy_free = nullptr; // [2 nf]
+    ddg::Allocs a_mesh;
+
+    // matrix (stage "matrix")
+    bool assembled = false;
+    int nnz = 0;
+    int *rowptr = nullptr, *col = nullptr;
+    double *val = nullptr, *b = nullptr;
+    double *g = nullptr;       // [n] Dirichlet values (0 on free nodes)
+    double bnorm = 0.0;
+    ddg::Allocs a_matrix;
+
+    // partition (stage "part")
+    int K = 0, delta = 0;
+    int *part = nullptr;                     // [nf]
+    int *mem_ptr = nullptr, *mem_idx = nullptr; // node -> subdomains (ascending)
+    int *mult = nullptr;                     // [nf]
+    int *sub_ptr = nullptr, *sub_idx = nullptr; // subdomain -> free ids (ascending)
+    int *inv_pos = nullptr;                  // mem slot -> position in sub_idx
+    long long sum_k = 0;
+    // local graphs
+    int *loc_ptr = nullptr, *loc_nint = nullptr, *loc_node = nullptr;
+    float2 *loc_xy = nullptr;                // (x - centre) / h_bar, FP32
+    int *nbr_ptr = nullptr;                  // per graph: n_loc + 1 offsets (graph i starts at loc_ptr[i] + i)
+    int *nbr_off = nullptr;                  // [K] start of graph i's neighbour slice
+    uint16_t *nbr = nullptr;
+    long long sum_loc = 0, sum_edges = 0;
+    int max_loc = 0, max_edges = 0;
+    int *lpt_order = nullptr;                // subdomains by decreasing graph size
+    double *A0 = nullptr, *A0inv = nullptr;  // [K*K]
+    ddg::Allocs a_part;
+
+    // preconditioner (stage "precond")
+    int kind = DDG_NONE;
+    uint32_t flags = 0;
+    const ddg_model *model = nullptr;
+    int *lu_perm = nullptr;     // [sum_k] band position -> position in sub_idx slice
+    int *lu_pos = nullptr;      // [sum_k] position in sub_idx slice -> band position
+    int *lu_bw = nullptr;       // [K]
+    long long *lu_off = nullptr; // [K+1] start of each band factor
+    double *lu_band = nullptr;
+    int lu_kmax = 0;
+    double *s = nullptr, *y = nullptr, *wc = nullptr, *corr = nullptr;
+    ddg::Allocs a_pre;
+
+    // Krylov workspace (stage "krylov")
+    int kr_m = 0;
+    double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kP = nullptr, *kQ = nullptr, *kscal = nullptr;
+    double *kpart = nullptr;   // block partials of reductions
+    int *kflag = nullptr;
+    ddg::Allocs a_kry;
+};
+
+namespace ddg {
+
+// allocation through the context's budget
+int32_t dmalloc(ddg_ctx *ctx, Allocs &a, void **p, size_t bytes);
+template <class T>
+int32_t dalloc(ddg_ctx *ctx, Allocs &a, T **p, size_t n) {
+    return dmalloc(ctx, a, reinterpret_cast<void **>(p), (n ? n : 1) * sizeof(T));
+}
+void dfree_all(ddg_ctx *ctx, Allocs &a);
+
+int32_t check_status(ddg_problem *p, const char *where);
+
+// primitives (prims.cu)
+int32_t scan_exclusive(ddg_ctx *ctx, const int *in, int *out, int n, int *total_host, cudaStream_t s);
+int32_t sort_points(ddg_ctx *ctx, const double *xy, int n, int axis, int *out_idx, cudaStream_t s);
+int32_t sort_pairs(ddg_ctx *ctx, const int *major, const int *minor, int n, int *out_idx, cudaStream_t s);
+int32_t reduce_sum(ddg_ctx *ctx, const double *in, int n, double *out_dev, cudaStream_t s);
+
+// stages
+int32_t mesh_build(ddg_problem *p, const uint8_t *dirichlet_host);
+int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal, const double *g_nodal);
+int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host);
+int32_t coarse_build(ddg_problem *p);
+int32_t lu_build(ddg_problem *p);
+int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s, bool corrections_only,
+                      double *corr_out, double *s_out);
+int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s);
+int32_t model_pack(ddg_model *m);
+int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
+int32_t dss_check_capacity(ddg_problem *p);
+int32_t model_xavier(ddg_model *m, uint64_t seed);
+int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
+int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
+                  ddg_solve_report *rep);
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// device helpers ---------------------------------------------------------
+__device__ __forceinline__ void raise_status(int *st, int bit) { atomicOr(st, bit); }
+
+template <class T>
+__device__ __forceinline__ void insertion_sort(T *a, int n) {
+    for (int i = 1; i < n; ++i) {
+        T v = a[i];
+        int j = i - 1;
+        while (j >= 0 && a[j] > v) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = v;
+    }
+}
+
+// deterministic block sum of one double per thread (blockDim.x multiple of 32, <= 1024)
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (warp == 0) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+}  // namespace ddg

@@ -1,0 +1,496 @@
+// Batched Deep Statistical Solver inference (Section III-B, Eqs. 18-22) for all
+// subdomain graphs of a decomposition in one launch (Section III-A, Eq. 14).
+//
+// One CTA runs one local graph through all kbar blocks; graphs are handed out
+// largest first.  Each thread owns up to P nodes for the whole inference and
+// keeps their latent vectors h (d = 10) and normalised residual c in registers.
+// The edge MLPs are evaluated in factorised form: with W1 = [Wa | Wb | We],
+//   W1 [h_j, h_l, e] + b1 = (Wa h_j + b1) + (Wb h_l) + We e,
+// so phase A of a block stores the per-node projections Wb_out h and Wb_in h
+// of every node in shared memory, and phase B forms every edge's hidden
+// pre-activation from the owner's Wa h_j + b1, the neighbour's stored
+// projection and the 3-vector edge feature; the second layer is applied once
+// to the per-node sum: sum_l (W2 relu(z_jl) + b2) = W2 sum_l relu(z_jl) + deg_j b2.
+// Edge features: d_jl = x_l - x_j scaled by h_bar for the out-message of j,
+// d_lj = x_j - x_l for its in-message, and the Euclidean norm.
+// Weights of the next block are fetched with a bulk tensor-memory-access copy
+// into the other half of a double buffer while the current block computes.
+#include "ddg_internal.cuh"
+
+#include <cmath>
+
+namespace ddg {
+
+// ---------------------------------------------------------------- packed layout (d = 10, rows padded to 12)
+constexpr int D = DSS_D;
+constexpr int DP = 12;
+// one edge MLP
+constexpr int PHI_WA = 0;                 // [D][DP] Wa^T
+constexpr int PHI_WB = PHI_WA + D * DP;   // [D][DP] Wb^T
+constexpr int PHI_WE = PHI_WB + D * DP;   // [3][DP] We^T
+constexpr int PHI_B1 = PHI_WE + 3 * DP;   // [DP]
+constexpr int PHI_W2 = PHI_B1 + DP;       // [D][DP] W2^T
+constexpr int PHI_B2 = PHI_W2 + D * DP;   // [DP]
+constexpr int PHI_SIZE = PHI_B2 + DP;     // 420
+// block
+constexpr int OFF_OUT = 0;
+constexpr int OFF_IN = PHI_SIZE;
+constexpr int OFF_PSI = 2 * PHI_SIZE;
+constexpr int PSI_W1 = 0;                      // [3D+1][DP]
+constexpr int PSI_B1 = PSI_W1 + (3 * D + 1) * DP;
+constexpr int PSI_W2 = PSI_B1 + DP;            // [D][DP]
+constexpr int PSI_B2 = PSI_W2 + D * DP;
+constexpr int PSI_SIZE = PSI_B2 + DP;          // 516
+constexpr int OFF_DEC = OFF_PSI + PSI_SIZE;
+constexpr int DEC_W1 = 0;                      // [D][DP]
+constexpr int DEC_B1 = DEC_W1 + D * DP;
+constexpr int DEC_W2 = DEC_B1 + DP;            // [DP]
+constexpr int DEC_B2 = DEC_W2 + DP;            // [4]
+constexpr int DEC_SIZE = DEC_B2 + 4;           // 148
+constexpr int BLOCK_FLOATS = OFF_DEC + DEC_SIZE;  // 1504
+constexpr int BLOCK_BYTES = BLOCK_FLOATS * 4;     // 6016, a multiple of 16
+static_assert(BLOCK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// flat layout offsets (row-major W[out][in]) of one block
+struct FlatOffsets {
+    int phi[2][4];  // W1, b1, W2, b2
+    int psi[4];
+    int dec[4];
+    int size;
+};
+
+static FlatOffsets flat_offsets(int d) {
+    FlatOffsets f{};
+    int o = 0;
+    for (int m = 0; m < 2; ++m) {
+        f.phi[m][0] = o; o += d * (2 * d + 3);
+        f.phi[m][1] = o; o += d;
+        f.phi[m][2] = o; o += d * d;
+        f.phi[m][3] = o; o += d;
+    }
+    f.psi[0] = o; o += d * (3 * d + 1);
+    f.psi[1] = o; o += d;
+    f.psi[2] = o; o += d * d;
+    f.psi[3] = o; o += d;
+    f.dec[0] = o; o += d * d;
+    f.dec[1] = o; o += d;
+    f.dec[2] = o; o += d;
+    f.dec[3] = o; o += 1;
+    f.size = o;
+    return f;
+}
+
+int32_t model_pack(ddg_model *m) {
+    // host-side repacking of the flat weights into the kernel's padded, transposed layout
+    const int kbar = m->kbar, d = m->d;
+    FlatOffsets fo = flat_offsets(d);
+    std::vector<float> flat(m->n_w), pk((size_t)kbar * BLOCK_FLOATS, 0.f);
+    DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < kbar; ++k) {
+        const float *w = flat.data() + (size_t)k * fo.size;
+        float *o = pk.data() + (size_t)k * BLOCK_FLOATS;
+        for (int mm = 0; mm < 2; ++mm) {
+            float *ph = o + (mm == 0 ? OFF_OUT : OFF_IN);
+            const float *W1 = w + fo.phi[mm][0], *b1 = w + fo.phi[mm][1], *W2 = w + fo.phi[mm][2],
+                        *b2 = w + fo.phi[mm][3];
+            const int in1 = 2 * D + 3;
+            for (int oo = 0; oo < D; ++oo) {
+                for (int i = 0; i < D; ++i) {
+                    ph[PHI_WA + i * DP + oo] = W1[oo * in1 + i];
+                    ph[PHI_WB + i * DP + oo] = W1[oo * in1 + D + i];
+                    ph[PHI_W2 + i * DP + oo] = W2[oo * D + i];
+                }
+                for (int i = 0; i < 3; ++i) ph[PHI_WE + i * DP + oo] = W1[oo * in1 + 2 * D + i];
+                ph[PHI_B1 + oo] = b1[oo];
+                ph[PHI_B2 + oo] = b2[oo];
+            }
+        }
+        float *ps = o + OFF_PSI;
+        const float *W1 = w + fo.psi[0], *b1 = w + fo.psi[1], *W2 = w + fo.psi[2], *b2 = w + fo.psi[3];
+        for (int oo = 0; oo < D; ++oo) {
+            for (int i = 0; i < 3 * D + 1; ++i) ps[PSI_W1 + i * DP + oo] = W1[oo * (3 * D + 1) + i];
+            for (int i = 0; i < D; ++i) ps[PSI_W2 + i * DP + oo] = W2[oo * D + i];
+            ps[PSI_B1 + oo] = b1[oo];
+            ps[PSI_B2 + oo] = b2[oo];
+        }
+        float *de = o + OFF_DEC;
+        const float *dW1 = w + fo.dec[0], *db1 = w + fo.dec[1], *dW2 = w + fo.dec[2], *db2 = w + fo.dec[3];
+        for (int oo = 0; oo < D; ++oo) {
+            for (int i = 0; i < D; ++i) de[DEC_W1 + i * DP + oo] = dW1[oo * D + i];
+            de[DEC_B1 + oo] = db1[oo];
+            de[DEC_W2 + oo] = dW2[oo];
+        }
+        de[DEC_B2] = db2[0];
+    }
+    DDG_TRY(dalloc(m->ctx, m->allocs, &m->packed, pk.size()));
+    DDG_CU(cudaMemcpy(m->packed, pk.data(), sizeof(float) * pk.size(), cudaMemcpyHostToDevice));
+    m->packed_per_block = BLOCK_FLOATS;
+    return DDG_OK;
+}
+
+// ---------------------------------------------------------------- SplitMix64 Xavier initialisation
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// value i of stream (seed, tag 2): Xavier-uniform for matrix entries, 0 for biases
+__global__ void k_xavier(float *w, int kbar, int d, uint64_t seed, const int *kind, const double *bound, int per_block) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)kbar * per_block) return;
+    int q = (int)(i % per_block);
+    if (!kind[q]) {
+        w[i] = 0.f;
+        return;
+    }
+    uint64_t key = splitmix_mix(seed ^ (2ull * 0xD1B54A32D192ED03ull));
+    uint64_t z = splitmix_mix(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+    double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    double a = bound[q];
+    w[i] = (float)(-a + 2.0 * a * u);
+}
+
+int32_t model_xavier(ddg_model *m, uint64_t seed) {
+    FlatOffsets fo = flat_offsets(m->d);
+    const int d = m->d;
+    std::vector<int> kind(fo.size, 0);
+    std::vector<double> bound(fo.size, 0.0);
+    auto mat = [&](int off, int fan_out, int fan_in) {
+        double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int q = 0; q < fan_out * fan_in; ++q) { kind[off + q] = 1; bound[off + q] = a; }
+    };
+    for (int mm = 0; mm < 2; ++mm) {
+        mat(fo.phi[mm][0], d, 2 * d + 3);
+        mat(fo.phi[mm][2], d, d);
+    }
+    mat(fo.psi[0], d, 3 * d + 1);
+    mat(fo.psi[2], d, d);
+    mat(fo.dec[0], d, d);
+    mat(fo.dec[2], 1, d);
+    int *dk;
+    double *db;
+    DDG_CU(cudaMalloc(&dk, sizeof(int) * fo.size));
+    DDG_CU(cudaMalloc(&db, sizeof(double) * fo.size));
+    DDG_CU(cudaMemcpy(dk, kind.data(), sizeof(int) * fo.size, cudaMemcpyHostToDevice));
+    DDG_CU(cudaMemcpy(db, bound.data(), sizeof(double) * fo.size, cudaMemcpyHostToDevice));
+    long long n = (long long)m->kbar * fo.size;
+    k_xavier<<<cdiv(n, 256), 256>>>(m->w, m->kbar, d, seed, dk, db, fo.size);
+    DDG_LAUNCH_CHECK();
+    DDG_CU(cudaDeviceSynchronize());
+    cudaFree(dk);
+    cudaFree(db);
+    return DDG_OK;
+}
+
+// ---------------------------------------------------------------- bulk copy + mbarrier helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// bounded wait on a phase of an mbarrier; returns false if the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- the kernel
+struct DssArgs {
+    const float *weights;   // packed, kbar blocks
+    int kbar;
+    float alpha;
+    const int *order;       // graph handed to CTA b
+    const int *loc_ptr, *loc_nint, *nbr_ptr, *nbr_off, *sub_ptr, *sub_idx;
+    const uint16_t *nbr;
+    const float2 *loc_xy;
+    const double *r;        // global residual (free nodes)
+    const double *s;        // |R_i r| per subdomain
+    double *corr;           // |R_i r| r~_i, sub_idx order
+    int nmax, emax;         // shared-memory capacity in nodes and edges
+    const int *stop;        // optional: skip all work when *stop != 0
+    int *status;
+};
+
+template <int NIN>
+__device__ __forceinline__ void mv_acc(float (&acc)[D], const float *WT, const float *x) {
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        const float4 w0 = *reinterpret_cast<const float4 *>(WT + i * DP);
+        const float4 w1 = *reinterpret_cast<const float4 *>(WT + i * DP + 4);
+        const float2 w2 = *reinterpret_cast<const float2 *>(WT + i * DP + 8);
+        const float xi = x[i];
+        acc[0] = fmaf(w0.x, xi, acc[0]);
+        acc[1] = fmaf(w0.y, xi, acc[1]);
+        acc[2] = fmaf(w0.z, xi, acc[2]);
+        acc[3] = fmaf(w0.w, xi, acc[3]);
+        acc[4] = fmaf(w1.x, xi, acc[4]);
+        acc[5] = fmaf(w1.y, xi, acc[5]);
+        acc[6] = fmaf(w1.z, xi, acc[6]);
+        acc[7] = fmaf(w1.w, xi, acc[7]);
+        acc[8] = fmaf(w2.x, xi, acc[8]);
+        acc[9] = fmaf(w2.y, xi, acc[9]);
+    }
+}
+
+__device__ __forceinline__ void load_vec(float (&v)[D], const float *src) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) v[o] = src[o];
+}
+
+// z = P_a + P_b(l) + We e  ->  S += relu(z)
+__device__ __forceinline__ void edge_msg(float (&S)[D], const float (&Pa)[D], const float *Pb, const float *We,
+                                         float ex, float ey, float en) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) {
+        float z = Pa[o] + Pb[o];
+        z = fmaf(We[o], ex, z);
+        z = fmaf(We[DP + o], ey, z);
+        z = fmaf(We[2 * DP + o], en, z);
+        S[o] += fmaxf(z, 0.f);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float *Wbuf = reinterpret_cast<float *>(smem + 128);
+    float *Pb = Wbuf + 2 * BLOCK_FLOATS;                          // [nmax][20]
+    float2 *xy = reinterpret_cast<float2 *>(Pb + (size_t)a.nmax * 2 * D);
+    uint16_t *nptr = reinterpret_cast<uint16_t *>(xy + a.nmax);  // [nmax + 1]
+    uint16_t *nbr = nptr + ((a.nmax + 1 + 7) & ~7);               // [emax]
+
+    if (a.stop && *a.stop) return;
+    const int tid = threadIdx.x;
+    const int g = a.order[blockIdx.x];
+    const int lp = a.loc_ptr[g];
+    const int nl = a.loc_ptr[g + 1] - lp;
+    const int k = a.loc_nint[g];
+    const int *gptr = a.nbr_ptr + lp + g;
+    const int ne = gptr[nl];
+    const int s0 = a.sub_ptr[g];
+    const double s = a.s[g];
+    if (s == 0.0) {  // zero local residual: no correction
+        for (int t = tid; t < k; t += DSS_THREADS) a.corr[s0 + t] = 0.0;
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) bulk_load(Wbuf, a.weights, BLOCK_BYTES, &bar[0]);
+    // stage the graph
+    for (int q = tid; q < nl; q += DSS_THREADS) xy[q] = a.loc_xy[lp + q];
+    for (int q = tid; q <= nl; q += DSS_THREADS) nptr[q] = (uint16_t)gptr[q];
+    const uint16_t *gn = a.nbr + a.nbr_off[g];
+    for (int e = tid; e < ne; e += DSS_THREADS) nbr[e] = gn[e];
+
+    float h[P][D];
+    float c[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        int j = p * DSS_THREADS + tid;
+        c[p] = (j < k) ? (float)(a.r[a.sub_idx[s0 + j]] / s) : 0.f;
+#pragma unroll
+        for (int o = 0; o < D; ++o) h[p][o] = 0.f;
+    }
+    const float alpha = a.alpha;
+    bool ok = true;
+
+    for (int blk = 0; blk < a.kbar; ++blk) {
+        const int buf = blk & 1;
+        const float *W = Wbuf + buf * BLOCK_FLOATS;
+        if (!mbar_wait(&bar[buf], (uint32_t)((blk >> 1) & 1))) ok = false;
+        __syncthreads();
+        if (tid == 0 && blk + 1 < a.kbar)
+            bulk_load(Wbuf + (buf ^ 1) * BLOCK_FLOATS, a.weights + (size_t)(blk + 1) * BLOCK_FLOATS, BLOCK_BYTES,
+                      &bar[buf ^ 1]);
+        // phase A: neighbour-side projections of every node
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            int j = p * DSS_THREADS + tid;
+            if (j < nl) {
+                float po[D], pi[D];
+#pragma unroll
+                for (int o = 0; o < D; ++o) { po[o] = 0.f; pi[o] = 0.f; }
+                mv_acc<D>(po, W + OFF_OUT + PHI_WB, h[p]);
+                mv_acc<D>(pi, W + OFF_IN + PHI_WB, h[p]);
+                float4 *dst = reinterpret_cast<float4 *>(Pb + (size_t)j * 2 * D);
+                dst[0] = make_float4(po[0], po[1], po[2], po[3]);
+                dst[1] = make_float4(po[4], po[5], po[6], po[7]);
+                dst[2] = make_float4(po[8], po[9], pi[0], pi[1]);
+                dst[3] = make_float4(pi[2], pi[3], pi[4], pi[5]);
+                dst[4] = make_float4(pi[6], pi[7], pi[8], pi[9]);
+            }
+        }
+        __syncthreads();
+        // phase B: messages, aggregation, node update
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            int j = p * DSS_THREADS + tid;
+            if (j < nl) {
+                const bool inner = j < k;
+                const float2 xj = xy[j];
+                float Pa_o[D], Pa_i[D], So[D], Si[D];
+                load_vec(Pa_o, W + OFF_OUT + PHI_B1);
+                load_vec(Pa_i, W + OFF_IN + PHI_B1);
+                mv_acc<D>(Pa_o, W + OFF_OUT + PHI_WA, h[p]);
+                mv_acc<D>(Pa_i, W + OFF_IN + PHI_WA, h[p]);
+#pragma unroll
+                for (int o = 0; o < D; ++o) { So[o] = 0.f; Si[o] = 0.f; }
+                int dout = 0, din = 0;
+                const int e0 = nptr[j], e1 = nptr[j + 1];
+                for (int e = e0; e < e1; ++e) {
+                    const int l = nbr[e];
+                    const float2 xl = xy[l];
+                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                    const float dn = sqrtf(dx * dx + dy * dy);
+                    const float *pbl = Pb + (size_t)l * 2 * D;
+                    if (l < k) {  // edge j -> l: out-message of j, feature d_jl = x_l - x_j
+                        edge_msg(So, Pa_o, pbl, W + OFF_OUT + PHI_WE, dx, dy, dn);
+                        ++dout;
+                    }
+                    if (inner) {  // edge l -> j: in-message of j, feature d_lj = x_j - x_l
+                        edge_msg(Si, Pa_i, pbl + D, W + OFF_IN + PHI_WE, -dx, -dy, dn);
+                        ++din;
+                    }
+                }
+                float phi_o[D], phi_i[D];
+                const float fo = (float)dout, fi = (float)din;
+#pragma unroll
+                for (int o = 0; o < D; ++o) {
+                    phi_o[o] = fo * W[OFF_OUT + PHI_B2 + o];
+                    phi_i[o] = fi * W[OFF_IN + PHI_B2 + o];
+                }
+                mv_acc<D>(phi_o, W + OFF_OUT + PHI_W2, So);
+                mv_acc<D>(phi_i, W + OFF_IN + PHI_W2, Si);
+                // Psi([h, c, phi_out, phi_in])
+                float hid[D];
+                load_vec(hid, W + OFF_PSI + PSI_B1);
+                mv_acc<D>(hid, W + OFF_PSI + PSI_W1, h[p]);
+                {
+                    float cc[1] = {c[p]};
+                    mv_acc<1>(hid, W + OFF_PSI + PSI_W1 + D * DP, cc);
+                }
+                mv_acc<D>(hid, W + OFF_PSI + PSI_W1 + (D + 1) * DP, phi_o);
+                mv_acc<D>(hid, W + OFF_PSI + PSI_W1 + (2 * D + 1) * DP, phi_i);
+#pragma unroll
+                for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+                float out[D];
+                load_vec(out, W + OFF_PSI + PSI_B2);
+                mv_acc<D>(out, W + OFF_PSI + PSI_W2, hid);
+#pragma unroll
+                for (int o = 0; o < D; ++o) h[p][o] = fmaf(alpha, out[o], h[p][o]);
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) raise_status(a.status, ST_TOO_LARGE);
+    // decoder of the last block on the unknowns (Eq. 22)
+    const float *W = Wbuf + ((a.kbar - 1) & 1) * BLOCK_FLOATS;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        int j = p * DSS_THREADS + tid;
+        if (j < k) {
+            float hid[D];
+            load_vec(hid, W + OFF_DEC + DEC_B1);
+            mv_acc<D>(hid, W + OFF_DEC + DEC_W1, h[p]);
+            float y = W[OFF_DEC + DEC_B2];
+#pragma unroll
+            for (int o = 0; o < D; ++o) y = fmaf(W[OFF_DEC + DEC_W2 + o], fmaxf(hid[o], 0.f), y);
+            a.corr[s0 + j] = s * (double)y;
+        }
+    }
+}
+
+static size_t dss_smem_bytes(int nmax, int emax) {
+    size_t b = 128 + 2 * (size_t)BLOCK_BYTES;
+    b += (size_t)nmax * 2 * D * sizeof(float);
+    b += (size_t)nmax * sizeof(float2);
+    b += (size_t)((nmax + 1 + 7) & ~7) * sizeof(uint16_t);
+    b += (size_t)emax * sizeof(uint16_t);
+    return (b + 127) & ~(size_t)127;
+}
+
+template <int P>
+static int32_t launch_p(const DssArgs &a, int K, size_t smem, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        configured = true;
+    }
+    k_dss<P><<<K, DSS_THREADS, smem, s>>>(a);
+    DDG_LAUNCH_CHECK();
+    return DDG_OK;
+}
+
+int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+    const ddg_model *m = p->model;
+    DssArgs a;
+    a.weights = m->packed;
+    a.kbar = m->kbar;
+    a.alpha = m->alpha;
+    a.order = p->lpt_order;
+    a.loc_ptr = p->loc_ptr;
+    a.loc_nint = p->loc_nint;
+    a.nbr_ptr = p->nbr_ptr;
+    a.nbr_off = p->nbr_off;
+    a.sub_ptr = p->sub_ptr;
+    a.sub_idx = p->sub_idx;
+    a.nbr = p->nbr;
+    a.loc_xy = p->loc_xy;
+    a.r = r;
+    a.s = p->s;
+    a.corr = p->corr;
+    a.nmax = p->max_loc;
+    a.emax = p->max_edges;
+    a.stop = stop;
+    a.status = p->d_status;
+    size_t smem = dss_smem_bytes(a.nmax, a.emax);
+    int P = cdiv(p->max_loc, DSS_THREADS);
+    switch (P) {
+        case 1: return launch_p<1>(a, p->K, smem, s);
+        case 2: return launch_p<2>(a, p->K, smem, s);
+        case 3: return launch_p<3>(a, p->K, smem, s);
+        case 4: return launch_p<4>(a, p->K, smem, s);
+        default: set_error("local graph too large for the GNN kernel"); return DDG_TOO_LARGE;
+    }
+}
+
+int32_t dss_check_capacity(ddg_problem *p) {
+    if (p->max_loc > DSS_MAX_NODES) {
+        set_error("local graph of " + std::to_string(p->max_loc) + " nodes exceeds the GNN kernel's " +
+                  std::to_string(DSS_MAX_NODES));
+        return DDG_TOO_LARGE;
+    }
+    if (p->max_edges > 65535 || dss_smem_bytes(p->max_loc, p->max_edges) > 227 * 1024) {
+        set_error("local graph does not fit the GNN kernel's shared memory");
+        return DDG_TOO_LARGE;
+    }
+    return DDG_OK;
+}
+
+}  // namespace ddg

@@ -1,0 +1,456 @@
+// Fine operator, preconditioner application and the flexible CG driver.
+//
+// Preconditioner (Section III-A): restriction with |R_i r| and the coarse
+// right-hand side R_0 r (Eq. 13's input), the coarse solve as a GEMV with the
+// setup's explicit inverse of A_0, the local solves (DSS inference, Eq. 14, or
+// band Cholesky, Eq. 7), and the gluing z = r_c + sum_i R_i^T |R_i r| r~_i
+// (Eq. 16) as a node-centric gather over each node's sorted subdomain list,
+// so every z_j is summed in a fixed order without atomics.
+//
+// Krylov: flexible CG with truncation m (Notay 2000): the new direction is
+// A-orthogonalised against the last m ones, p_k = z_k - sum_j (z_k.q_j)/(p_j.q_j) p_j,
+// alpha = (p_k.r_k)/(p_k.q_k).  With m = 1 and a fixed SPD preconditioner it
+// generates the iterates of Algorithm 1.  All vectors and dot products are
+// FP64; every reduction uses a fixed grid and a fixed summation tree, so a
+// solve is bitwise reproducible.  Scalars stay on the device; the host only
+// polls a stop flag every few iterations.
+#include "ddg_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace ddg {
+
+constexpr int KT = 256;            // threads per block of the vector kernels
+constexpr int RB = 296;            // fixed grid of the reductions (2 x 148 SMs)
+constexpr int MAXM = 16;           // largest truncation
+constexpr int POLL = 4;            // iterations between stop-flag polls
+
+// scalar slots (kscal) and flags (kflag)
+enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT = 8 + 2 * MAXM };
+enum { F_STOP = 0, F_ITERS = 1, F_COUNT = 2 };
+
+// ------------------------------------------------------------------ SpMV
+__global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                             const double *__restrict__ val, const double *__restrict__ x,
+                                             double *__restrict__ y, int n, const double *__restrict__ rdot,
+                                             double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (stop && *stop) return;
+    int i = blockIdx.x * KT + threadIdx.x;
+    double pq = 0.0, pr = 0.0;
+    if (i < n) {
+        double acc = 0.0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * x[col[e]];
+        y[i] = acc;
+        if (part) {
+            double xi = x[i];
+            pq = xi * acc;
+            pr = xi * rdot[i];
+        }
+    }
+    if (part) {
+        pq = block_sum(pq, sh);
+        pr = block_sum(pr, sh);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = pq;
+            part[gridDim.x + blockIdx.x] = pr;
+        }
+    }
+}
+
+int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
+    k_spmv<<<cdiv(p->nf, KT), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf, nullptr, nullptr, nullptr);
+    DDG_LAUNCH_CHECK();
+    return DDG_OK;
+}
+
+// ------------------------------------------------------------------ preconditioner pieces
+__global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *sub_idx, const int *mult,
+                                                 const double *r, double *s_out, double *y_out, const int *stop) {
+    __shared__ double sh[32];
+    if (stop && *stop) return;
+    int i = blockIdx.x;
+    double ss = 0.0, yy = 0.0;
+    for (int q = sub_ptr[i] + threadIdx.x; q < sub_ptr[i + 1]; q += KT) {
+        int j = sub_idx[q];
+        double v = r[j];
+        ss += v * v;
+        yy += v * (1.0 / mult[j]);
+    }
+    ss = block_sum(ss, sh);
+    yy = block_sum(yy, sh);
+    if (threadIdx.x == 0) {
+        s_out[i] = sqrt(ss);
+        y_out[i] = yy;
+    }
+}
+
+// w = A0inv y, one warp per row
+__global__ void k_coarse_gemv(const double *Ainv, const double *y, double *w, int K, const int *stop) {
+    if (stop && *stop) return;
+    int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= K) return;
+    const double *a = Ainv + (long long)row * K;
+    double acc = 0.0;
+    for (int c = lane; c < K; c += 32) acc += a[c] * y[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) w[row] = acc;
+}
+
+__global__ void __launch_bounds__(KT) k_prolong(const int *mptr, const int *midx, const int *inv_pos,
+                                                const int *mult, const double *corr, const double *w, int nf,
+                                                int coarse, int pou, double *z, const int *stop) {
+    if (stop && *stop) return;
+    int j = blockIdx.x * KT + threadIdx.x;
+    if (j >= nf) return;
+    double inv_m = 1.0 / mult[j];
+    double acc = 0.0;
+    int q0 = mptr[j], q1 = mptr[j + 1];
+    if (coarse)
+        for (int q = q0; q < q1; ++q) acc += inv_m * w[midx[q]];
+    for (int q = q0; q < q1; ++q) {
+        double c = corr[inv_pos[q]];
+        acc += pou ? c * inv_m : c;
+    }
+    z[j] = acc;
+}
+
+__global__ void k_copy(const double *a, double *b, int n, const int *stop) {
+    if (stop && *stop) return;
+    int i = blockIdx.x * KT + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+// launches the preconditioner's kernels; ev_local (optional) brackets the local-solve kernel;
+// *launches (optional) is increased by the number of kernels launched
+static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStream_t s, const int *stop,
+                            bool prolong, cudaEvent_t *ev_local = nullptr, int *launches = nullptr) {
+    int nl = 0;
+    if (p->kind == DDG_NONE) {
+        if (prolong) {
+            k_copy<<<cdiv(p->nf, KT), KT, 0, s>>>(r, z, p->nf, stop);
+            DDG_LAUNCH_CHECK();
+            nl = 1;
+        }
+        if (launches) *launches += nl;
+        return DDG_OK;
+    }
+    const int K = p->K;
+    k_restrict<<<K, KT, 0, s>>>(p->sub_ptr, p->sub_idx, p->mult, r, p->s, p->y, stop);
+    DDG_LAUNCH_CHECK();
+    ++nl;
+    const bool coarse = (p->flags & DDG_COARSE) != 0;
+    if (coarse && prolong) {
+        k_coarse_gemv<<<cdiv(K, 8), 256, 0, s>>>(p->A0inv, p->y, p->wc, K, stop);
+        DDG_LAUNCH_CHECK();
+        ++nl;
+    }
+    if (ev_local) DDG_CU(cudaEventRecord(ev_local[0], s));
+    if (p->kind == DDG_DDM_GNN) {
+        DDG_TRY(dss_launch_args(p, r, stop, s));
+    } else {
+        DDG_TRY(lu_apply_launch(p, r, stop, s));
+    }
+    if (ev_local) DDG_CU(cudaEventRecord(ev_local[1], s));
+    ++nl;
+    if (prolong) {
+        k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->mult, p->corr, p->wc,
+                                                 p->nf, coarse ? 1 : 0, (p->flags & DDG_POU_PROLONG) ? 1 : 0, z,
+                                                 stop);
+        DDG_LAUNCH_CHECK();
+        ++nl;
+    }
+    if (launches) *launches += nl;
+    return DDG_OK;
+}
+
+int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s, bool corrections_only,
+                      double *corr_out, double *s_out) {
+    DDG_TRY(precond_core(p, r, z, s, nullptr, !corrections_only));
+    if (corrections_only && p->kind != DDG_NONE) {
+        DDG_CU(cudaMemcpyAsync(corr_out, p->corr, sizeof(double) * p->sum_k, cudaMemcpyDeviceToDevice, s));
+        DDG_CU(cudaMemcpyAsync(s_out, p->s, sizeof(double) * p->K, cudaMemcpyDeviceToDevice, s));
+    }
+    return DDG_OK;
+}
+
+// ------------------------------------------------------------------ FCG kernels
+struct Window {
+    int W;            // directions to orthogonalise against
+    int slot[MAXM];   // their ring slots, oldest first
+    int snew;         // slot of the new direction
+};
+
+__global__ void __launch_bounds__(KT) k_dot(const double *a, const double *b, int n, double *part) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) v += a[i] * b[i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// d_j = z . Q[slot_j], block partials part[j * RB + block]
+__global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *Q, long long ld, Window win, int n,
+                                                 double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double acc[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) {
+        double zi = z[i];
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (j < win.W) acc[j] += zi * Q[win.slot[j] * ld + i];
+    }
+    for (int j = 0; j < win.W; ++j) {
+        double v = block_sum(acc[j], sh);
+        if (threadIdx.x == 0) part[j * RB + blockIdx.x] = v;
+    }
+}
+
+// beta_j = d_j / (p_j . q_j)
+__global__ void k_beta(const double *part, Window win, double *scal, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    for (int j = 0; j < win.W; ++j) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < RB; b += blockDim.x) v += part[j * RB + b];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) scal[S_BETA + j] = v / scal[S_PQ + win.slot[j]];
+    }
+}
+
+// P[snew] = z - sum_j beta_j P[slot_j]  (P[snew] may be one of the P[slot_j]: read before write, same index)
+__global__ void __launch_bounds__(KT) k_pupdate(const double *z, double *P, long long ld, Window win, int n,
+                                                const double *scal, const int *stop) {
+    if (*stop) return;
+    long long i = (long long)blockIdx.x * KT + threadIdx.x;
+    if (i >= n) return;
+    double v = z[i];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+        if (j < win.W) v -= scal[S_BETA + j] * P[win.slot[j] * ld + i];
+    P[win.snew * ld + i] = v;
+}
+
+// alpha = (p.r) / (p.q); breakdown if p.q <= 0 or not finite
+__global__ void k_alpha(const double *part, int nb, Window win, double *scal, int *flag) {
+    __shared__ double sh[32];
+    if (flag[F_STOP]) return;
+    double pq = 0.0, pr = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        pq += part[b];
+        pr += part[nb + b];
+    }
+    pq = block_sum(pq, sh);
+    pr = block_sum(pr, sh);
+    if (threadIdx.x == 0) {
+        double al = pr / pq;
+        if (!(pq > 0.0) || !isfinite(al)) {
+            flag[F_STOP] = 2;
+            return;
+        }
+        scal[S_PQ + win.snew] = pq;
+        scal[S_ALPHA] = al;
+    }
+}
+
+__global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p, const double *q, int n,
+                                           const double *scal, double *part, const int *stop) {
+    __shared__ double sh[32];
+    if (*stop) return;
+    double al = scal[S_ALPHA];
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) {
+        x[i] += al * p[i];
+        double ri = r[i] - al * q[i];
+        r[i] = ri;
+        v += ri * ri;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__global__ void k_conv(const double *part, double *scal, int *flag, double tol) {
+    __shared__ double sh[32];
+    if (flag[F_STOP]) return;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < RB; b += blockDim.x) v += part[b];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        double rel = sqrt(v) / scal[S_BNORM];
+        scal[S_REL] = rel;
+        flag[F_ITERS] += 1;
+        if (!isfinite(rel)) flag[F_STOP] = 2;
+        else if (rel < tol) flag[F_STOP] = 1;
+    }
+}
+
+__global__ void k_sumsq_final(const double *part, int nb, double *out) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) *out = sqrt(v);
+}
+
+__global__ void k_residual(const double *b, const double *Ax, double *res, int n) {
+    int i = blockIdx.x * KT + threadIdx.x;
+    if (i < n) res[i] = b[i] - Ax[i];
+}
+
+__global__ void k_full_solution(const double *x, const double *g, const int *free_id, int n, double *u) {
+    int a = blockIdx.x * KT + threadIdx.x;
+    if (a >= n) return;
+    int f = free_id[a];
+    u[a] = f >= 0 ? x[f] : g[a];
+}
+
+static int32_t norm2(ddg_problem *p, const double *v, double *out_dev, cudaStream_t s) {
+    k_dot<<<RB, KT, 0, s>>>(v, v, p->nf, p->kpart);
+    DDG_LAUNCH_CHECK();
+    k_sumsq_final<<<1, KT, 0, s>>>(p->kpart, RB, out_dev);
+    DDG_LAUNCH_CHECK();
+    return DDG_OK;
+}
+
+int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
+                  ddg_solve_report *rep) {
+    ddg_ctx *c = p->ctx;
+    cudaStream_t s = c->stream;
+    const int nf = p->nf;
+    if (m < 1 || m > MAXM) {
+        set_error("m_trunc must be in [1, 16]");
+        return DDG_INVALID_ARG;
+    }
+    if (p->kr_m != m) {
+        dfree_all(c, p->a_kry);
+        p->kr_m = 0;
+    }
+    if (p->kr_m == 0) {
+        DDG_TRY(dalloc(c, p->a_kry, &p->kx, nf));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kr, nf));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kz, std::max(nf, p->n)));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)std::max(MAXM * RB, 2 * cdiv(nf, KT)) + 8));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
+        p->kr_m = m;
+    }
+    double *x = p->kx, *r = p->kr, *z = p->kz, *P = p->kP, *Q = p->kQ, *scal = p->kscal, *part = p->kpart;
+    int *flag = p->kflag;
+    const long long ld = nf;
+    DDG_CU(cudaMemsetAsync(flag, 0, sizeof(int) * F_COUNT, s));
+    DDG_CU(cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, s));
+    // x0, r0 = b - A x0
+    if (x0) {
+        DDG_CU(cudaMemcpyAsync(x, x0, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+        DDG_TRY(spmv(p, x, z, s));
+        k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, r, nf);
+        DDG_LAUNCH_CHECK();
+    } else {
+        DDG_CU(cudaMemsetAsync(x, 0, sizeof(double) * nf, s));
+        DDG_CU(cudaMemcpyAsync(r, p->b, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+    }
+    DDG_TRY(norm2(p, p->b, scal + S_BNORM, s));
+
+    cudaEvent_t e0, e1;
+    DDG_CU(cudaEventCreate(&e0));
+    DDG_CU(cudaEventCreate(&e1));
+    // per-iteration events of one polling window: precond start/end, local kernel start/end
+    cudaEvent_t ev[POLL][4];
+    for (int q = 0; q < POLL; ++q)
+        for (int k = 0; k < 4; ++k) DDG_CU(cudaEventCreate(&ev[q][k]));
+    double pre_ms = 0.0, loc_ms = 0.0;
+    int loc_launches = 0, launches = 0, in_window = 0;
+    auto drain = [&](int cnt) {
+        for (int q = 0; q < cnt; ++q) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[q][0], ev[q][1]);
+            if (p->kind != DDG_NONE) cudaEventElapsedTime(&b, ev[q][2], ev[q][3]);
+            pre_ms += a;
+            loc_ms += b;
+        }
+    };
+    DDG_CU(cudaEventRecord(e0, s));
+    const int nb_spmv = cdiv(nf, KT);
+    int hflag[F_COUNT] = {0, 0};
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        Window win{};
+        win.W = std::min(it, m);
+        for (int j = 0; j < win.W; ++j) win.slot[j] = (it - win.W + j) % m;
+        win.snew = it % m;
+        cudaEvent_t *evq = ev[in_window];
+        DDG_CU(cudaEventRecord(evq[0], s));
+        DDG_TRY(precond_core(p, r, z, s, flag, true, p->kind != DDG_NONE ? evq + 2 : nullptr, &launches));
+        DDG_CU(cudaEventRecord(evq[1], s));
+        if (p->kind != DDG_NONE) ++loc_launches;
+        ++in_window;
+        if (win.W > 0) {
+            k_multidot<<<RB, KT, 0, s>>>(z, Q, ld, win, nf, part, flag);
+            k_beta<<<1, KT, 0, s>>>(part, win, scal, flag);
+            launches += 2;
+            DDG_LAUNCHES(2);
+        }
+        k_pupdate<<<cdiv(nf, KT), KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
+        double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
+        k_spmv<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part, flag);
+        k_alpha<<<1, KT, 0, s>>>(part, nb_spmv, win, scal, flag);
+        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part, flag);
+        k_conv<<<1, KT, 0, s>>>(part, scal, flag, rtol);
+        launches += 5;
+        DDG_LAUNCHES(5);
+        if (in_window == POLL || it + 1 == max_iter) {
+            DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+            DDG_CU(cudaStreamSynchronize(s));
+            drain(in_window);
+            in_window = 0;
+            if (hflag[F_STOP]) break;
+        }
+    }
+    DDG_CU(cudaEventRecord(e1, s));
+    DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+    double hs[S_COUNT];
+    DDG_CU(cudaMemcpyAsync(hs, scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+    // true residual |b - A x| / |b|
+    DDG_TRY(spmv(p, x, z, s));
+    k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, z, nf);
+    DDG_LAUNCH_CHECK();
+    double *tr = scal + S_COUNT;
+    DDG_TRY(norm2(p, z, tr, s));
+    double htr = 0.0;
+    DDG_CU(cudaMemcpyAsync(&htr, tr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (x_host) {
+        k_full_solution<<<cdiv(p->n, KT), KT, 0, s>>>(x, p->g, p->free_id, p->n, z);
+        DDG_LAUNCH_CHECK();
+        DDG_CU(cudaMemcpyAsync(x_host, z, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s));
+    }
+    DDG_CU(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int q = 0; q < POLL; ++q)
+        for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[q][k]);
+    ddg_solve_report rp{};
+    rp.iterations = hflag[F_ITERS];
+    rp.rel_residual = hs[S_REL];
+    rp.true_rel_residual = htr / hs[S_BNORM];
+    rp.solve_ms = ms;
+    rp.precond_ms = pre_ms;
+    rp.local_ms = loc_ms;
+    rp.local_launches = loc_launches;
+    rp.launches = launches;
+    rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
+    if (rep) *rep = rp;
+    if (rp.status == DDG_BREAKDOWN) set_error("FCG breakdown: p.q <= 0 or a non-finite scalar");
+    if (rp.status == DDG_NOT_CONVERGED) set_error("FCG reached max_iter");
+    return rp.status;
+}
+
+}  // namespace ddg

@@ -1,0 +1,147 @@
+"""GPU SpMV, DDM-LU and DDM-GNN preconditioners against the oracle (Eqs. 7, 13-16; Section III-B)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ddm, dss, partition as pt
+from helpers import gpu_setup, oracle_setup, rel
+
+pytestmark = pytest.mark.gpu
+
+KBAR, D = 30, 10
+
+
+@pytest.fixture(scope="module")
+def ddg():
+    import paper_2402_08296_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(ddg):
+    c = ddg.ddg_create(0)
+    yield c
+    ddg.ddg_destroy(c)
+
+
+def _dev(torch, a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float64)).cuda()
+
+
+@pytest.mark.parametrize("name,seed", [("square2k", 0), ("star20000", 2)])
+def test_spmv(ddg, ctx, torch, name, seed):
+    w = synth.workload(name, seed)
+    P, _ = oracle_setup(w.mesh, w.coeffs, 1, 0)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs)
+    try:
+        x = synth.residual_vector(P.n_free, seed + 10)
+        xd = _dev(torch, x)
+        yd = torch.zeros_like(xd)
+        ddg.ddg_apply_A(p, xd, yd)
+        torch.cuda.synchronize()
+        ref = P.A @ x
+        assert np.max(np.abs(yd.cpu().numpy() - ref)) <= 1e-13 * np.abs(P.A.data).max() * np.abs(x).max() * 8
+    finally:
+        ddg.ddg_problem_destroy(p)
+
+
+@pytest.mark.parametrize("name,seed,K,delta,coarse", [("square2k", 0, 4, 1, True), ("star20000", 1, 20, 2, True),
+                                                      ("star20000", 3, 20, 2, False)])
+def test_ddm_lu_precondition(ddg, ctx, torch, name, seed, K, delta, coarse):
+    w = synth.workload(name, seed)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    asm = ddm.TwoLevelASM(P, Dd, coarse=coarse)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE if coarse else 0)
+        r = synth.residual_vector(P.n_free, seed + 20)
+        rd = _dev(torch, r)
+        zd = torch.zeros_like(rd)
+        ddg.ddg_precondition(p, rd, zd)
+        torch.cuda.synchronize()
+        assert rel(zd.cpu().numpy(), asm.apply_lu(r)) < 1e-11
+    finally:
+        ddg.ddg_problem_destroy(p)
+
+
+def _weights(seed, bias):
+    return synth.dss_weights(KBAR, D, seed, bias_scale=bias)
+
+
+@pytest.mark.parametrize("name,seed,K,delta,alpha,bias", [
+    ("square2k", 0, 4, 1, 1e-3, 0.0),       # the paper's alpha and initialisation
+    ("square2k", 1, 4, 1, 0.05, 0.1),       # stronger nonlinearity, nonzero biases
+    ("star20000", 2, 20, 2, 0.02, 0.1),     # ~1,300-node graphs with halo, ragged sizes
+])
+def test_dss_local_corrections(ddg, ctx, torch, name, seed, K, delta, alpha, bias):
+    w = synth.workload(name, seed)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    W = _weights(seed, bias)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    m = ddg.ddg_model_create(ctx, KBAR, D, alpha, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        r = synth.residual_vector(P.n_free, seed + 30)
+        rd = _dev(torch, r)
+        sk = sum(len(S) for S in Dd.sets)
+        corr = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        s = torch.zeros(K, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr, s = corr.cpu().numpy(), s.cpu().numpy()
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        off = 0
+        for i, S in enumerate(Dd.sets):
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            assert abs(s[i] - si) <= 1e-14 * si
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, D, alpha, hbar)
+            got = corr[off:off + len(S)]
+            off += len(S)
+            assert rel(got, ref) < 1e-4, (i, rel(got, ref))
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+@pytest.mark.parametrize("pou", [False, True])
+def test_ddm_gnn_precondition(ddg, ctx, torch, pou):
+    w = synth.workload("square2k", 4)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, 4, 1)
+    W = _weights(4, 0.1)
+    alpha = 0.05
+    gnn = ddm.DDMGNN(ddm.TwoLevelASM(P, Dd), W, KBAR, D, alpha, pou=pou)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    m = ddg.ddg_model_create(ctx, KBAR, D, alpha, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE | (ddg.DDG_POU_PROLONG if pou else 0))
+        r = synth.residual_vector(P.n_free, 44)
+        rd = _dev(torch, r)
+        zd = torch.zeros_like(rd)
+        ddg.ddg_precondition(p, rd, zd)
+        torch.cuda.synchronize()
+        assert rel(zd.cpu().numpy(), gnn.apply(r)) < 1e-4
+        # zero residual: zero local corrections, zero coarse term
+        ddg.ddg_precondition(p, torch.zeros_like(rd), zd)
+        torch.cuda.synchronize()
+        assert float(zd.abs().max()) == 0.0
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+def test_model_xavier_init_matches_splitmix_stream(ddg, ctx):
+    m = ddg.ddg_model_create(ctx, 3, D, 1e-3, None, seed=123)
+    try:
+        got = ddg.ddg_model_get_weights(m, 3 * synth.n_weights_per_block(D))
+        assert np.array_equal(got, synth.dss_weights(3, D, 123))
+    finally:
+        ddg.ddg_model_destroy(m)
