@@ -180,6 +180,22 @@ int32_t ddg_local_corrections(ddg_problem *p, const double *r_dev, double *corr_
 /* y = A_ff x for device vectors of n_free FP64. */
 int32_t ddg_apply_A(ddg_problem *p, const double *x_dev, double *y_dev, ddg_stream stream);
 
+/* y = A_ff x and *xy_dev = x . y (FP64, deterministic) without allocating any
+ * device memory, for callers that cannot call cudaMalloc (inside a stream
+ * capture owned by someone else, under an allocator that forbids allocations
+ * after start-up, or in a loop that cannot afford an allocation).  No passage
+ * of the paper corresponds to this call; it exists for those callers.
+ * x_dev, y_dev: n_free FP64 device vectors; xy_dev: one FP64 on the device.
+ * Scratch is a 512 KiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits; n_free may be at most
+ * 16,777,216 (DDG_TOO_LARGE beyond).  The first call on a device looks up the
+ * array's device address, so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and their dot
+ * products are then wrong; order them on one stream.  Errors:
+ * DDG_INVALID_ARG, DDG_TOO_LARGE, DDG_CUDA_ERROR. */
+int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, double *y_dev, double *xy_dev,
+                                ddg_stream stream);
+
 /* Solve A_ff x = b_f by flexible CG (truncation m_trunc >= 1; m_trunc = 1
  * reproduces PCG for a fixed SPD preconditioner) from x0 (host, n_free, or
  * NULL = 0) until |r| / |b| < rtol or max_iter iterations.  x_host[n_nodes]

@@ -80,6 +80,7 @@ _SIGS = {
     "ddg_precondition": [_p, _p, _p, _p],
     "ddg_local_corrections": [_p, _p, _p, _p, _p],
     "ddg_apply_A": [_p, _p, _p, _p],
+    "ddg_apply_A_dot_noalloc": [_p, _p, _p, _p, _p],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
 }
 for _name, _args in _SIGS.items():
@@ -286,6 +287,12 @@ def ddg_local_corrections(p, r_dev, corr_dev, s_dev, stream=None) -> None:
 
 def ddg_apply_A(p, x_dev, y_dev, stream=None) -> None:
     _check(lib.ddg_apply_A(p, _dev(x_dev), _dev(y_dev), _stream(stream, x_dev, y_dev)), "ddg_apply_A")
+
+
+def ddg_apply_A_dot_noalloc(p, x_dev, y_dev, xy_dev, stream=None) -> None:
+    """y = A x and x . y into the one-element device tensor xy_dev, with no device allocation."""
+    _check(lib.ddg_apply_A_dot_noalloc(p, _dev(x_dev), _dev(y_dev), _dev(xy_dev), _stream(stream, x_dev, y_dev)),
+           "ddg_apply_A_dot_noalloc")
 
 
 def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: bool = True):
