@@ -20,7 +20,9 @@
  *    keeps ownership.  Host arrays passed out are written, never kept.
  *  - Device pointers (ddg_precondition, ddg_apply_A, ddg_local_corrections)
  *    are borrowed: they must live on the context's device and are used in
- *    stream order on the stream given (NULL = the context's own stream).
+ *    stream order on the stream given.  NULL selects the context's own
+ *    stream, which is non-blocking: it does not synchronise with the legacy
+ *    default stream, so pass cudaStreamLegacy to run on that one.
  *  - Indices are int32, zero-based.  "free" nodes are the mesh nodes that are
  *    not Dirichlet nodes, numbered in ascending mesh order.
  *  - A context and everything created from it is not thread-safe.

@@ -117,17 +117,25 @@ def _dev(x):
     return _p(x.data_ptr())
 
 
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
+
+
 def _stream(stream, *tensors):
-    """The stream to launch on: the given one, else torch's current stream when torch tensors are passed."""
+    """The stream to launch on: the given one, else torch's current stream when torch tensors are passed.
+
+    Handle 0 (torch's legacy default stream) is passed as cudaStreamLegacy, because the C ABI
+    reads NULL as "the context's own stream", which does not synchronise with the default stream.
+    """
     if stream is None:
         for t in tensors:
             if hasattr(t, "data_ptr") and hasattr(t, "device"):
                 import torch
-                return _p(torch.cuda.current_stream(t.device).cuda_stream)
-        return None
-    if isinstance(stream, int):
-        return _p(stream)
-    return _p(stream.cuda_stream)
+                stream = torch.cuda.current_stream(t.device)
+                break
+        else:
+            return None
+    h = stream if isinstance(stream, int) else stream.cuda_stream
+    return _p(h if h else CUDA_STREAM_LEGACY)
 
 
 def ddg_last_error() -> str:

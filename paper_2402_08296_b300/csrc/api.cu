@@ -309,6 +309,10 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
         DDG_TRY(lu_build(p));
     } else {
         DDG_TRY(dss_check_capacity(p));
+        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_D * p->sum_loc));
+        DDG_TRY(dalloc(c, p->a_pre, &p->dss_c, p->sum_loc));
+        p->kind = kind;
+        DDG_TRY(dss_autotune(p));
     }
     p->kind = kind;
     return DDG_OK;

@@ -75,6 +75,7 @@ struct ddg_model {
     float *w = nullptr;       // flat weights as given (device)
     float *packed = nullptr;  // per-block padded layout read by the GNN kernel (device)
     size_t packed_per_block = 0;
+    std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
     ddg::Allocs allocs;
 };
 
@@ -137,6 +138,8 @@ struct ddg_problem {
     double *lu_band = nullptr;
     int lu_kmax = 0;
     double *s = nullptr, *y = nullptr, *wc = nullptr, *corr = nullptr;
+    int dss_sched = 0;          // GNN schedule: 0 = one persistent launch, 1 = one launch per block
+    float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedule 1)
     ddg::Allocs a_pre;
 
     // Krylov workspace (stage "krylov")
@@ -177,6 +180,7 @@ int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s);
 int32_t model_pack(ddg_model *m);
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t dss_check_capacity(ddg_problem *p);
+int32_t dss_autotune(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,

@@ -124,6 +124,7 @@ int32_t model_pack(ddg_model *m) {
     }
     DDG_TRY(dalloc(m->ctx, m->allocs, &m->packed, pk.size()));
     DDG_CU(cudaMemcpy(m->packed, pk.data(), sizeof(float) * pk.size(), cudaMemcpyHostToDevice));
+    m->packed_host = pk;
     m->packed_per_block = BLOCK_FLOATS;
     return DDG_OK;
 }
@@ -426,6 +427,196 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- per-block schedule
+// The same inference as k_dss, one launch per message-passing block: the
+// block's weights travel as a kernel parameter, so every weight operand of the
+// FMAs is read from the constant bank instead of shared memory, and shared
+// memory holds only the neighbour projections.  Latents persist in global
+// memory between launches (structure of arrays, h[o * n_total + node]); the
+// graph (coordinates, adjacency) is read through the L1 cache.
+struct __align__(16) BlockWeights {
+    float w[BLOCK_FLOATS];
+};
+
+struct DssStepArgs {
+    const int *order;
+    const int *loc_ptr, *loc_nint, *nbr_ptr, *nbr_off, *sub_ptr, *sub_idx;
+    const uint16_t *nbr;
+    const float2 *loc_xy;
+    const double *r, *s;
+    double *corr;
+    float *h;          // [D][n_total]
+    float *c;          // [n_total]
+    long long n_total;
+    float alpha;
+    int first, last;
+    const int *stop;
+};
+
+template <int NIN, int OFF>
+__device__ __forceinline__ void mvc_acc(float (&acc)[D], const BlockWeights &W, const float *x) {
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        const float xi = x[i];
+#pragma unroll
+        for (int o = 0; o < D; ++o) acc[o] = fmaf(W.w[OFF + i * DP + o], xi, acc[o]);
+    }
+}
+
+template <int OFF>
+__device__ __forceinline__ void loadc(float (&v)[D], const BlockWeights &W) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) v[o] = W.w[OFF + o];
+}
+
+template <int OFF>
+__device__ __forceinline__ void edge_msg_c(float (&S)[D], const float (&Pa)[D], const float *Pb, const BlockWeights &W,
+                                           float ex, float ey, float en) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) {
+        float z = Pa[o] + Pb[o];
+        z = fmaf(W.w[OFF + o], ex, z);
+        z = fmaf(W.w[OFF + DP + o], ey, z);
+        z = fmaf(W.w[OFF + 2 * DP + o], en, z);
+        S[o] += fmaxf(z, 0.f);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(DSS_THREADS, 1) k_dss_step(const __grid_constant__ BlockWeights W,
+                                                              const __grid_constant__ DssStepArgs a) {
+    extern __shared__ __align__(16) float Pb[];  // [n_loc][2 D]
+    if (a.stop && *a.stop) return;
+    const int tid = threadIdx.x;
+    const int g = a.order[blockIdx.x];
+    const int lp = a.loc_ptr[g];
+    const int nl = a.loc_ptr[g + 1] - lp;
+    const int k = a.loc_nint[g];
+    const int s0 = a.sub_ptr[g];
+    const double s = a.s[g];
+    if (s == 0.0) {
+        if (a.last)
+            for (int t = tid; t < k; t += DSS_THREADS) a.corr[s0 + t] = 0.0;
+        return;
+    }
+    const int *gptr = a.nbr_ptr + lp + g;
+    const uint16_t *gn = a.nbr + a.nbr_off[g];
+    const float2 *xy = a.loc_xy + lp;
+    float h[P][D];
+    float c[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = p * DSS_THREADS + tid;
+        if (j < nl) {
+            if (a.first) {
+                c[p] = (j < k) ? (float)(a.r[a.sub_idx[s0 + j]] / s) : 0.f;
+                a.c[lp + j] = c[p];
+#pragma unroll
+                for (int o = 0; o < D; ++o) h[p][o] = 0.f;
+            } else {
+                c[p] = a.c[lp + j];
+#pragma unroll
+                for (int o = 0; o < D; ++o) h[p][o] = a.h[o * a.n_total + lp + j];
+            }
+        } else {
+            c[p] = 0.f;
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[p][o] = 0.f;
+        }
+    }
+    // phase A
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = p * DSS_THREADS + tid;
+        if (j < nl) {
+            float po[D], pi[D];
+#pragma unroll
+            for (int o = 0; o < D; ++o) { po[o] = 0.f; pi[o] = 0.f; }
+            mvc_acc<D, OFF_OUT + PHI_WB>(po, W, h[p]);
+            mvc_acc<D, OFF_IN + PHI_WB>(pi, W, h[p]);
+            float4 *dst = reinterpret_cast<float4 *>(Pb + (size_t)j * 2 * D);
+            dst[0] = make_float4(po[0], po[1], po[2], po[3]);
+            dst[1] = make_float4(po[4], po[5], po[6], po[7]);
+            dst[2] = make_float4(po[8], po[9], pi[0], pi[1]);
+            dst[3] = make_float4(pi[2], pi[3], pi[4], pi[5]);
+            dst[4] = make_float4(pi[6], pi[7], pi[8], pi[9]);
+        }
+    }
+    __syncthreads();
+    // phase B
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = p * DSS_THREADS + tid;
+        if (j < nl) {
+            const bool inner = j < k;
+            const float2 xj = xy[j];
+            float Pa_o[D], Pa_i[D], So[D], Si[D];
+            loadc<OFF_OUT + PHI_B1>(Pa_o, W);
+            loadc<OFF_IN + PHI_B1>(Pa_i, W);
+            mvc_acc<D, OFF_OUT + PHI_WA>(Pa_o, W, h[p]);
+            mvc_acc<D, OFF_IN + PHI_WA>(Pa_i, W, h[p]);
+#pragma unroll
+            for (int o = 0; o < D; ++o) { So[o] = 0.f; Si[o] = 0.f; }
+            int dout = 0, din = 0;
+            const int e0 = gptr[j], e1 = gptr[j + 1];
+            for (int e = e0; e < e1; ++e) {
+                const int l = gn[e];
+                const float2 xl = xy[l];
+                const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                const float dn = sqrtf(dx * dx + dy * dy);
+                const float *pbl = Pb + (size_t)l * 2 * D;
+                if (l < k) {
+                    edge_msg_c<OFF_OUT + PHI_WE>(So, Pa_o, pbl, W, dx, dy, dn);
+                    ++dout;
+                }
+                if (inner) {
+                    edge_msg_c<OFF_IN + PHI_WE>(Si, Pa_i, pbl + D, W, -dx, -dy, dn);
+                    ++din;
+                }
+            }
+            float phi_o[D], phi_i[D];
+            const float fo = (float)dout, fi = (float)din;
+#pragma unroll
+            for (int o = 0; o < D; ++o) {
+                phi_o[o] = fo * W.w[OFF_OUT + PHI_B2 + o];
+                phi_i[o] = fi * W.w[OFF_IN + PHI_B2 + o];
+            }
+            mvc_acc<D, OFF_OUT + PHI_W2>(phi_o, W, So);
+            mvc_acc<D, OFF_IN + PHI_W2>(phi_i, W, Si);
+            float hid[D];
+            loadc<OFF_PSI + PSI_B1>(hid, W);
+            mvc_acc<D, OFF_PSI + PSI_W1>(hid, W, h[p]);
+            {
+                float cc[1] = {c[p]};
+                mvc_acc<1, OFF_PSI + PSI_W1 + D * DP>(hid, W, cc);
+            }
+            mvc_acc<D, OFF_PSI + PSI_W1 + (D + 1) * DP>(hid, W, phi_o);
+            mvc_acc<D, OFF_PSI + PSI_W1 + (2 * D + 1) * DP>(hid, W, phi_i);
+#pragma unroll
+            for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+            float out[D];
+            loadc<OFF_PSI + PSI_B2>(out, W);
+            mvc_acc<D, OFF_PSI + PSI_W2>(out, W, hid);
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[p][o] = fmaf(a.alpha, out[o], h[p][o]);
+            if (a.last) {
+                if (inner) {
+                    float dh[D];
+                    loadc<OFF_DEC + DEC_B1>(dh, W);
+                    mvc_acc<D, OFF_DEC + DEC_W1>(dh, W, h[p]);
+                    float y = W.w[OFF_DEC + DEC_B2];
+#pragma unroll
+                    for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], fmaxf(dh[o], 0.f), y);
+                    a.corr[s0 + j] = s * (double)y;
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < D; ++o) a.h[o * a.n_total + lp + j] = h[p][o];
+            }
+        }
+    }
+}
+
 static size_t dss_smem_bytes(int nmax, int emax) {
     size_t b = 128 + 2 * (size_t)BLOCK_BYTES;
     b += (size_t)nmax * 2 * D * sizeof(float);
@@ -447,7 +638,57 @@ static int32_t launch_p(const DssArgs &a, int K, size_t smem, cudaStream_t s) {
     return DDG_OK;
 }
 
+template <int P>
+static int32_t launch_steps(ddg_problem *p, const DssStepArgs &base, size_t smem, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss_step<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        configured = true;
+    }
+    const ddg_model *m = p->model;
+    for (int blk = 0; blk < m->kbar; ++blk) {
+        DssStepArgs a = base;
+        a.first = blk == 0;
+        a.last = blk == m->kbar - 1;
+        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(m->packed_host.data()) + blk;
+        k_dss_step<P><<<p->K, DSS_THREADS, smem, s>>>(*W, a);
+    }
+    DDG_LAUNCHES(m->kbar);
+    return DDG_OK;
+}
+
+int32_t dss_step_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+    DssStepArgs a;
+    a.order = p->lpt_order;
+    a.loc_ptr = p->loc_ptr;
+    a.loc_nint = p->loc_nint;
+    a.nbr_ptr = p->nbr_ptr;
+    a.nbr_off = p->nbr_off;
+    a.sub_ptr = p->sub_ptr;
+    a.sub_idx = p->sub_idx;
+    a.nbr = p->nbr;
+    a.loc_xy = p->loc_xy;
+    a.r = r;
+    a.s = p->s;
+    a.corr = p->corr;
+    a.h = p->dss_h;
+    a.c = p->dss_c;
+    a.n_total = p->sum_loc;
+    a.alpha = p->model->alpha;
+    a.first = a.last = 0;
+    a.stop = stop;
+    size_t smem = (size_t)p->max_loc * 2 * D * sizeof(float);
+    switch (cdiv(p->max_loc, DSS_THREADS)) {
+        case 1: return launch_steps<1>(p, a, smem, s);
+        case 2: return launch_steps<2>(p, a, smem, s);
+        case 3: return launch_steps<3>(p, a, smem, s);
+        case 4: return launch_steps<4>(p, a, smem, s);
+        default: set_error("local graph too large for the GNN kernel"); return DDG_TOO_LARGE;
+    }
+}
+
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+    if (p->dss_sched == 1) return dss_step_launch(p, r, stop, s);
     const ddg_model *m = p->model;
     DssArgs a;
     a.weights = m->packed;

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 namespace ddg {
 
@@ -25,10 +26,11 @@ constexpr int KT = 256;            // threads per block of the vector kernels
 constexpr int RB = 296;            // fixed grid of the reductions (2 x 148 SMs)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
+constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
 
 // scalar slots (kscal) and flags (kflag)
 enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT = 8 + 2 * MAXM };
-enum { F_STOP = 0, F_ITERS = 1, F_COUNT = 2 };
+enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
 
 // ------------------------------------------------------------------ SpMV
 __global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
@@ -176,12 +178,71 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
     return DDG_OK;
 }
 
+// Picks the faster GNN schedule for this decomposition (one persistent launch,
+// or one launch per block with the weights in the constant bank) by timing
+// both on the right-hand side; DDG_GNN_SCHEDULE=0/1 in the environment forces one.
+int32_t dss_autotune(ddg_problem *p) {
+    const char *env = getenv("DDG_GNN_SCHEDULE");
+    if (env && (env[0] == '0' || env[0] == '1')) {
+        p->dss_sched = env[0] - '0';
+        return DDG_OK;
+    }
+    cudaStream_t s = p->ctx->stream;
+    cudaEvent_t e0, e1;
+    DDG_CU(cudaEventCreate(&e0));
+    DDG_CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 0;
+    for (int sched = 0; sched < 2; ++sched) {
+        p->dss_sched = sched;
+        DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
+        DDG_CU(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 2; ++rep) DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
+        DDG_CU(cudaEventRecord(e1, s));
+        DDG_CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DDG_CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            pick = sched;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->dss_sched = pick;
+    return check_status(p, "GNN schedule selection");
+}
+
 // ------------------------------------------------------------------ FCG kernels
+// Each reduction writes one partial per block; the last block to finish (ticket
+// counter, reset by that block) sums the partials in block order and derives the
+// iteration's scalars, so a solve stays bitwise reproducible without extra launches.
 struct Window {
     int W;            // directions to orthogonalise against
     int slot[MAXM];   // their ring slots, oldest first
     int snew;         // slot of the new direction
 };
+
+__device__ __forceinline__ bool last_block(int *ticket) {
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(reinterpret_cast<unsigned int *>(ticket), 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// sum of part[0..n) by one warp in a fixed order (valid in every lane)
+__device__ __forceinline__ double warp_sum_parts(const double *part, int n, int lane) {
+    double v = 0.0;
+    for (int b = lane; b < n; b += 32) v += part[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 __global__ void __launch_bounds__(KT) k_dot(const double *a, const double *b, int n, double *part) {
     __shared__ double sh[32];
@@ -191,11 +252,11 @@ __global__ void __launch_bounds__(KT) k_dot(const double *a, const double *b, in
     if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
-// d_j = z . Q[slot_j], block partials part[j * RB + block]
+// d_j = z . Q[slot_j]; the last block forms beta_j = d_j / (p_j . q_j)
 __global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *Q, long long ld, Window win, int n,
-                                                 double *part, const int *stop) {
+                                                 double *part, double *scal, int *flag) {
     __shared__ double sh[32];
-    if (*stop) return;
+    if (flag[F_STOP]) return;
     double acc[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
@@ -209,59 +270,82 @@ __global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *
         double v = block_sum(acc[j], sh);
         if (threadIdx.x == 0) part[j * RB + blockIdx.x] = v;
     }
-}
-
-// beta_j = d_j / (p_j . q_j)
-__global__ void k_beta(const double *part, Window win, double *scal, const int *stop) {
-    __shared__ double sh[32];
-    if (*stop) return;
-    for (int j = 0; j < win.W; ++j) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < RB; b += blockDim.x) v += part[j * RB + b];
-        v = block_sum(v, sh);
-        if (threadIdx.x == 0) scal[S_BETA + j] = v / scal[S_PQ + win.slot[j]];
+    if (last_block(&flag[F_T_MD])) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int j = warp; j < win.W; j += KT / 32) {
+            double d = warp_sum_parts(part + j * RB, RB, lane);
+            if (lane == 0) scal[S_BETA + j] = d / scal[S_PQ + win.slot[j]];
+        }
+        if (threadIdx.x == 0) flag[F_T_MD] = 0;
     }
 }
 
 // P[snew] = z - sum_j beta_j P[slot_j]  (P[snew] may be one of the P[slot_j]: read before write, same index)
 __global__ void __launch_bounds__(KT) k_pupdate(const double *z, double *P, long long ld, Window win, int n,
-                                                const double *scal, const int *stop) {
-    if (*stop) return;
-    long long i = (long long)blockIdx.x * KT + threadIdx.x;
-    if (i >= n) return;
-    double v = z[i];
+                                                const double *scal, const int *flag) {
+    if (flag[F_STOP]) return;
+    __shared__ double beta[MAXM];
+    if (threadIdx.x < MAXM) beta[threadIdx.x] = threadIdx.x < win.W ? scal[S_BETA + threadIdx.x] : 0.0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
+        double v = z[i];
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-        if (j < win.W) v -= scal[S_BETA + j] * P[win.slot[j] * ld + i];
-    P[win.snew * ld + i] = v;
+        for (int j = 0; j < MAXM; ++j)
+            if (j < win.W) v -= beta[j] * P[win.slot[j] * ld + i];
+        P[win.snew * ld + i] = v;
+    }
 }
 
-// alpha = (p.r) / (p.q); breakdown if p.q <= 0 or not finite
-__global__ void k_alpha(const double *part, int nb, Window win, double *scal, int *flag) {
+// q = A p with the partial dots p.q and p.r; the last block forms alpha = (p.r) / (p.q)
+__global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                 const double *__restrict__ val, const double *__restrict__ p,
+                                                 double *__restrict__ q, int n, const double *__restrict__ r,
+                                                 double *part, Window win, double *scal, int *flag) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
+    int i = blockIdx.x * KT + threadIdx.x;
     double pq = 0.0, pr = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        pq += part[b];
-        pr += part[nb + b];
+    if (i < n) {
+        double acc = 0.0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * p[col[e]];
+        q[i] = acc;
+        double pi = p[i];
+        pq = pi * acc;
+        pr = pi * r[i];
     }
     pq = block_sum(pq, sh);
     pr = block_sum(pr, sh);
     if (threadIdx.x == 0) {
-        double al = pr / pq;
-        if (!(pq > 0.0) || !isfinite(al)) {
-            flag[F_STOP] = 2;
-            return;
+        part[blockIdx.x] = pq;
+        part[gridDim.x + blockIdx.x] = pr;
+    }
+    if (last_block(&flag[F_T_SP])) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __shared__ double sums[2];
+        if (warp < 2) {
+            double v = warp_sum_parts(part + warp * gridDim.x, gridDim.x, lane);
+            if (lane == 0) sums[warp] = v;
         }
-        scal[S_PQ + win.snew] = pq;
-        scal[S_ALPHA] = al;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double spq = sums[0], spr = sums[1];
+            double al = spr / spq;
+            if (!(spq > 0.0) || !isfinite(al)) {
+                flag[F_STOP] = 2;
+            } else {
+                scal[S_PQ + win.snew] = spq;
+                scal[S_ALPHA] = al;
+            }
+            flag[F_T_SP] = 0;
+        }
     }
 }
 
+// x += alpha p; r -= alpha q; the last block forms |r| / |b| and raises the stop flag
 __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p, const double *q, int n,
-                                           const double *scal, double *part, const int *stop) {
+                                           double *scal, double *part, int *flag, double tol) {
     __shared__ double sh[32];
-    if (*stop) return;
+    if (flag[F_STOP]) return;
     double al = scal[S_ALPHA];
     double v = 0.0;
     for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) {
@@ -272,20 +356,18 @@ __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-
-__global__ void k_conv(const double *part, double *scal, int *flag, double tol) {
-    __shared__ double sh[32];
-    if (flag[F_STOP]) return;
-    double v = 0.0;
-    for (int b = threadIdx.x; b < RB; b += blockDim.x) v += part[b];
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        double rel = sqrt(v) / scal[S_BNORM];
-        scal[S_REL] = rel;
-        flag[F_ITERS] += 1;
-        if (!isfinite(rel)) flag[F_STOP] = 2;
-        else if (rel < tol) flag[F_STOP] = 1;
+    if (last_block(&flag[F_T_XR])) {
+        if (threadIdx.x < 32) {
+            double rr = warp_sum_parts(part, RB, threadIdx.x);
+            if (threadIdx.x == 0) {
+                double rel = sqrt(rr) / scal[S_BNORM];
+                scal[S_REL] = rel;
+                flag[F_ITERS] += 1;
+                if (!isfinite(rel)) flag[F_STOP] = 2;
+                else if (rel < tol) flag[F_STOP] = 1;
+                flag[F_T_XR] = 0;
+            }
+        }
     }
 }
 
@@ -337,7 +419,7 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
         DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
         DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
         DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)std::max(MAXM * RB, 2 * cdiv(nf, KT)) + 8));
+        DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)(MAXM * RB + 2 * cdiv(nf, KT) + RB + 8)));
         DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
         p->kr_m = m;
     }
@@ -378,7 +460,8 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
     };
     DDG_CU(cudaEventRecord(e0, s));
     const int nb_spmv = cdiv(nf, KT);
-    int hflag[F_COUNT] = {0, 0};
+    const long long off_sp = OFF_MD + MAXM * RB, off_rr = off_sp + 2LL * nb_spmv;
+    int hflag[F_COUNT] = {0, 0, 0, 0, 0};
     int it = 0;
     for (; it < max_iter; ++it) {
         Window win{};
@@ -391,20 +474,17 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
         DDG_CU(cudaEventRecord(evq[1], s));
         if (p->kind != DDG_NONE) ++loc_launches;
         ++in_window;
-        if (win.W > 0) {
-            k_multidot<<<RB, KT, 0, s>>>(z, Q, ld, win, nf, part, flag);
-            k_beta<<<1, KT, 0, s>>>(part, win, scal, flag);
-            launches += 2;
-            DDG_LAUNCHES(2);
-        }
-        k_pupdate<<<cdiv(nf, KT), KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
         double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
-        k_spmv<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part, flag);
-        k_alpha<<<1, KT, 0, s>>>(part, nb_spmv, win, scal, flag);
-        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part, flag);
-        k_conv<<<1, KT, 0, s>>>(part, scal, flag, rtol);
-        launches += 5;
-        DDG_LAUNCHES(5);
+        if (win.W > 0) {
+            k_multidot<<<RB, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
+            launches += 1;
+            DDG_LAUNCHES(1);
+        }
+        k_pupdate<<<RB, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
+        k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
+        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
+        launches += 3;
+        DDG_LAUNCHES(3);
         if (in_window == POLL || it + 1 == max_iter) {
             DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
             DDG_CU(cudaStreamSynchronize(s));

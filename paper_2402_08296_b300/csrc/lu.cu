@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(LU_T) k_lu_fill(const int *sub_ptr, const int 
     }
 }
 
-// right-looking band Cholesky, one CTA per subdomain
+// right-looking band Cholesky, one CTA per subdomain; the diagonal slot of
+// every row receives 1 / L[r][r] so that the solves multiply instead of divide
 __global__ void __launch_bounds__(LU_T) k_lu_factor(const int *sub_ptr, const int *bw_arr, const long long *off,
                                                     double *band, int *st) {
     __shared__ double dinv;
@@ -158,9 +159,8 @@ __global__ void __launch_bounds__(LU_T) k_lu_factor(const int *sub_ptr, const in
                 bad = 1;
                 d = 1.0;
             }
-            d = sqrt(d);
-            B[(long long)c * w + bw] = d;
-            dinv = 1.0 / d;
+            dinv = 1.0 / sqrt(d);
+            B[(long long)c * w + bw] = dinv;
         }
         __syncthreads();
         const int rmax = min(c + bw, k - 1);
@@ -179,44 +179,78 @@ __global__ void __launch_bounds__(LU_T) k_lu_factor(const int *sub_ptr, const in
     if (threadIdx.x == 0 && bad) raise_status(st, ST_BAD_INPUT);
 }
 
-// forward and backward band solves, one warp per subdomain; corr in sub_idx order
-__global__ void __launch_bounds__(32) k_lu_apply(const int *sub_ptr, const int *sub_idx, const int *lu_pos,
-                                                 const int *bw_arr, const long long *off, const double *band,
-                                                 const double *r, const double *s, double *corr, const int *stop) {
+// forward and backward band solves, one CTA per subdomain, rows in tiles of 32:
+// a warp solves each 32 x 32 diagonal tile, the whole CTA applies the band
+// entries outside it; corr is written in sub_idx order
+constexpr int LU_TILE = 32;
+
+__global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int *sub_idx, const int *lu_pos,
+                                                   const int *bw_arr, const long long *off, const double *band,
+                                                   const double *r, const double *s, double *corr, const int *stop) {
     extern __shared__ double yv[];
     if (stop && *stop) return;
     const int i = blockIdx.x;
     const int s0 = sub_ptr[i], k = sub_ptr[i + 1] - s0;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bw = bw_arr[i], w = bw + 1;
     const double *B = band + off[i];
-    for (int t = lane; t < k; t += 32) yv[lu_pos[s0 + t]] = r[sub_idx[s0 + t]];
-    __syncwarp();
     if (s[i] == 0.0) {
-        for (int t = lane; t < k; t += 32) corr[s0 + t] = 0.0;
+        for (int t = tid; t < k; t += LU_T) corr[s0 + t] = 0.0;
         return;
     }
-    // L y = b, row-oriented
-    for (int row = 0; row < k; ++row) {
-        const double *Lr = B + (long long)row * w;
-        int c0 = max(0, row - bw);
-        double acc = 0.0;
-        for (int c = c0 + lane; c < row; c += 32) acc += Lr[c - row + bw] * yv[c];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) yv[row] = (yv[row] - acc) / Lr[bw];
-        __syncwarp();
+    for (int t = tid; t < k; t += LU_T) yv[lu_pos[s0 + t]] = r[sub_idx[s0 + t]];
+    __syncthreads();
+    // L y = b
+    for (int r0 = 0; r0 < k; r0 += LU_TILE) {
+        const int nrow = min(LU_TILE, k - r0);
+        for (int rr = warp; rr < nrow; rr += LU_T / 32) {
+            const int row = r0 + rr;
+            const double *Lr = B + (long long)row * w;
+            double acc = 0.0;
+            for (int c = max(0, row - bw) + lane; c < r0; c += 32) acc += Lr[c - row + bw] * yv[c];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) yv[row] -= acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int row = r0 + lane;
+            const double *Lr = B + (long long)row * w;
+            double y = lane < nrow ? yv[row] : 0.0;
+            for (int j = 0; j < nrow; ++j) {
+                if (lane == j) y *= Lr[bw];
+                const double xj = __shfl_sync(0xffffffffu, y, j);
+                if (lane > j && lane < nrow && lane - j <= bw) y -= Lr[(r0 + j) - row + bw] * xj;
+            }
+            if (lane < nrow) yv[row] = y;
+        }
+        __syncthreads();
     }
-    // L^T x = y, column-oriented: after x_row is known, remove its term from the rows above
-    for (int row = k - 1; row >= 0; --row) {
-        const double *Lr = B + (long long)row * w;
-        double xr = yv[row] / Lr[bw];
-        __syncwarp();
-        int c0 = max(0, row - bw);
-        for (int c = c0 + lane; c < row; c += 32) yv[c] -= Lr[c - row + bw] * xr;
-        if (lane == 0) yv[row] = xr;
-        __syncwarp();
+    // L^T x = y, tiles from the bottom
+    for (int r0 = ((k - 1) / LU_TILE) * LU_TILE; r0 >= 0; r0 -= LU_TILE) {
+        const int nrow = min(LU_TILE, k - r0);
+        if (warp == 0) {
+            const int row = r0 + lane;
+            double y = lane < nrow ? yv[row] : 0.0;
+            const double dinv = lane < nrow ? B[(long long)row * w + bw] : 0.0;
+            for (int j = nrow - 1; j >= 0; --j) {
+                if (lane == j) y *= dinv;
+                const double xj = __shfl_sync(0xffffffffu, y, j);
+                if (lane < j && j - lane <= bw) y -= B[(long long)(r0 + j) * w + (row - (r0 + j) + bw)] * xj;
+            }
+            if (lane < nrow) yv[row] = y;
+        }
+        __syncthreads();
+        for (int c = max(0, r0 - bw) + tid; c < r0; c += LU_T) {
+            double acc = 0.0;
+            for (int qq = 0; qq < nrow; ++qq) {
+                const int q = r0 + qq;
+                if (q - c <= bw) acc += B[(long long)q * w + (c - q + bw)] * yv[q];
+            }
+            yv[c] -= acc;
+        }
+        __syncthreads();
     }
-    for (int t = lane; t < k; t += 32) corr[s0 + t] = yv[lu_pos[s0 + t]];
+    for (int t = tid; t < k; t += LU_T) corr[s0 + t] = yv[lu_pos[s0 + t]];
 }
 
 int32_t lu_build(ddg_problem *p) {
@@ -266,7 +300,7 @@ int32_t lu_build(ddg_problem *p) {
 }
 
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
-    k_lu_apply<<<p->K, 32, sizeof(double) * p->lu_kmax, s>>>(p->sub_ptr, p->sub_idx, p->lu_pos, p->lu_bw,
+    k_lu_apply<<<p->K, LU_T, sizeof(double) * p->lu_kmax, s>>>(p->sub_ptr, p->sub_idx, p->lu_pos, p->lu_bw,
                                                              p->lu_off, p->lu_band, r, p->s, p->corr, stop);
     DDG_LAUNCH_CHECK();
     return DDG_OK;

@@ -451,40 +451,69 @@ __global__ void __launch_bounds__(LG_T) k_graph_fill(const int *sub_ptr, const i
 }
 
 // ------------------------------------------------------------------ coarse space
-constexpr int COARSE_TAB = 96;
+// A_0[a][b] = sum_{j in S_a} sum_{l in row j, b in sets(l)} A_jl / (m_j m_l), one CTA per row a:
+// the CTA first collects the subdomains b that can appear (a bitmap over K), then
+// one warp per b sums over S_a with a fixed lane assignment and a fixed shuffle tree.
+constexpr int CO_T = 256;
+constexpr int CO_MAX_NB = 256;
 
-__global__ void k_coarse_rows(const int *sub_ptr, const int *sub_idx, const int *rowptr, const int *col,
-                              const double *val, const int *mptr, const int *midx, const int *mult, int K,
-                              double *A0, int *st) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= K) return;
-    int key[COARSE_TAB];
-    double acc[COARSE_TAB];
-    int m = 0;
-    for (int q = sub_ptr[a]; q < sub_ptr[a + 1]; ++q) {
+__global__ void __launch_bounds__(CO_T) k_coarse_rows(const int *sub_ptr, const int *sub_idx, const int *rowptr,
+                                                      const int *col, const double *val, const int *mptr,
+                                                      const int *midx, const int *mult, int K, double *A0,
+                                                      int *st) {
+    extern __shared__ unsigned int bits[];  // ceil(K / 32) words
+    __shared__ int nb_list[CO_MAX_NB];
+    __shared__ int nb_count;
+    const int a = blockIdx.x;
+    const int words = (K + 31) / 32;
+    for (int q = threadIdx.x; q < words; q += CO_T) bits[q] = 0u;
+    if (threadIdx.x == 0) nb_count = 0;
+    __syncthreads();
+    const int q0 = sub_ptr[a], q1 = sub_ptr[a + 1];
+    for (int q = q0 + threadIdx.x; q < q1; q += CO_T) {
         int j = sub_idx[q];
-        double wa = 1.0 / mult[j];
         for (int e = rowptr[j]; e < rowptr[j + 1]; ++e) {
             int l = col[e];
-            double v = wa * val[e] * (1.0 / mult[l]);
             for (int r = mptr[l]; r < mptr[l + 1]; ++r) {
                 int b = midx[r];
-                int u = 0;
-                while (u < m && key[u] != b) ++u;
-                if (u == m) {
-                    if (m == COARSE_TAB) {
-                        raise_status(st, ST_TOO_LARGE);
-                        return;
-                    }
-                    key[m] = b;
-                    acc[m] = 0.0;
-                    ++m;
-                }
-                acc[u] += v;
+                atomicOr(&bits[b >> 5], 1u << (b & 31));
             }
         }
     }
-    for (int u = 0; u < m; ++u) A0[(long long)a * K + key[u]] = acc[u];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int wd = 0; wd < words; ++wd) {
+            unsigned int m = bits[wd];
+            while (m) {
+                int bit = __ffs(m) - 1;
+                m &= m - 1;
+                if (c < CO_MAX_NB) nb_list[c] = wd * 32 + bit;
+                ++c;
+            }
+        }
+        nb_count = c;
+        if (c > CO_MAX_NB) raise_status(st, ST_TOO_LARGE);
+    }
+    __syncthreads();
+    const int nbc = min(nb_count, CO_MAX_NB);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int u = warp; u < nbc; u += CO_T / 32) {
+        const int b = nb_list[u];
+        double acc = 0.0;
+        for (int q = q0 + lane; q < q1; q += 32) {
+            int j = sub_idx[q];
+            double wa = 1.0 / mult[j];
+            for (int e = rowptr[j]; e < rowptr[j + 1]; ++e) {
+                int l = col[e];
+                bool hit = false;
+                for (int r = mptr[l]; r < mptr[l + 1]; ++r) hit |= midx[r] == b;
+                if (hit) acc += wa * val[e] * (1.0 / mult[l]);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) A0[(long long)a * K + b] = acc;
+    }
 }
 
 __global__ void k_gj_pivot(const double *A, int K, int k, double *prow, double *fcol, int *st) {
@@ -518,8 +547,13 @@ int32_t coarse_build(ddg_problem *p) {
     DDG_TRY(dalloc(c, p->a_part, &p->A0, (size_t)K * K));
     DDG_TRY(dalloc(c, p->a_part, &p->A0inv, (size_t)K * K));
     DDG_CU(cudaMemsetAsync(p->A0, 0, sizeof(double) * K * K, s));
-    k_coarse_rows<<<cdiv(K, 64), 64, 0, s>>>(p->sub_ptr, p->sub_idx, p->rowptr, p->col, p->val, p->mem_ptr,
-                                              p->mem_idx, p->mult, K, p->A0, p->d_status);
+    size_t co_smem = sizeof(unsigned int) * ((K + 31) / 32);
+    if (co_smem > 48 * 1024) {
+        set_error("K too large for the coarse-matrix kernel");
+        return DDG_TOO_LARGE;
+    }
+    k_coarse_rows<<<K, CO_T, co_smem, s>>>(p->sub_ptr, p->sub_idx, p->rowptr, p->col, p->val, p->mem_ptr,
+                                           p->mem_idx, p->mult, K, p->A0, p->d_status);
     DDG_LAUNCH_CHECK();
     DDG_TRY(check_status(p, "coarse matrix"));
     DDG_CU(cudaMemcpyAsync(p->A0inv, p->A0, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));

@@ -1,0 +1,135 @@
+"""Parity at the full benchmark sizes, in the benchmark's launch configuration, on sampled outputs.
+
+* star100k: the benchmark workload (~100k nodes, K = 100, 2-layer overlap, kbar = 30, d = 10).
+* star1m:   the large single solve (~1M nodes, K ~ 1,000).
+The oracle recomputes what it can afford: the whole matrix and partition,
+the DDM-LU preconditioner (star100k), and the GNN corrections of sampled
+subdomains (the largest, the smallest and a few others).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ddm, dss, fem, partition as pt
+from helpers import gpu_setup, rel
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
+KBAR, DLAT, ALPHA = 30, 10, 1e-3
+
+
+def bench_weights():
+    if os.path.exists(WEIGHTS):
+        return np.load(WEIGHTS).astype(np.float32)
+    return synth.dss_weights(KBAR, DLAT, 0)
+
+
+@pytest.fixture(scope="module")
+def ddg():
+    import paper_2402_08296_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(ddg):
+    c = ddg.ddg_create(0)
+    yield c
+    ddg.ddg_destroy(c)
+
+
+@pytest.fixture(scope="module", params=["star100k", "star1m"])
+def full(request, ddg, ctx):
+    w = synth.workload(request.param, 0)
+    P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
+    D = pt.decompose(P, w.K, w.overlap)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, w.K, w.overlap)
+    yield request.param, w, P, D, p
+    ddg.ddg_problem_destroy(p)
+
+
+def test_full_matrix_and_partition(ddg, full):
+    name, w, P, D, p = full
+    rowptr, col, val, b = ddg.ddg_matrix_download(p)
+    assert np.array_equal(rowptr, P.A.indptr) and np.array_equal(col, P.A.indices)
+    assert np.max(np.abs(val - P.A.data)) <= 1e-12 * np.abs(P.A.data).max()
+    assert np.max(np.abs(b - P.b)) <= 1e-12 * np.abs(P.b).max()
+    part, sub_ptr, sub_idx, mult = ddg.ddg_partition_download(p)
+    assert np.array_equal(part, D.part) and np.array_equal(mult, D.mult)
+    assert np.array_equal(sub_idx, np.concatenate(D.sets))
+    info = ddg.ddg_problem_info(p)
+    assert info["max_loc"] <= 2048
+
+
+def _sample(D, count=4):
+    sizes = np.array([len(S) for S in D.sets])
+    pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    rng = np.random.default_rng(5)
+    while len(pick) < min(count, len(D.sets)):
+        pick.add(int(rng.integers(len(D.sets))))
+    return sorted(pick)
+
+
+def test_full_gnn_corrections_sampled(ddg, ctx, torch, full):
+    name, w, P, D, p = full
+    W = bench_weights()
+    m = ddg.ddg_model_create(ctx, KBAR, DLAT, ALPHA, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        r = synth.residual_vector(P.n_free, 77)
+        rd = torch.as_tensor(r).cuda()
+        corr = torch.zeros(sum(len(S) for S in D.sets), dtype=torch.float64, device="cuda")
+        s = torch.zeros(len(D.sets), dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr = corr.cpu().numpy()
+        offs = np.concatenate([[0], np.cumsum([len(S) for S in D.sets])])
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        for i in _sample(D):
+            S = D.sets[i]
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, DLAT, ALPHA, hbar)
+            assert rel(corr[offs[i]:offs[i + 1]], ref) < 1e-4, (name, i)
+    finally:
+        ddg.ddg_setup_precond(p, ddg.DDG_NONE)
+        ddg.ddg_model_destroy(m)
+
+
+def test_full_ddm_lu(ddg, torch, full):
+    name, w, P, D, p = full
+    if name != "star100k":
+        pytest.skip("the oracle's sparse LU of 1,000 subdomains is checked on the 100k workload")
+    asm = ddm.TwoLevelASM(P, D)
+    ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE)
+    r = synth.residual_vector(P.n_free, 78)
+    rd = torch.as_tensor(r).cuda()
+    zd = torch.zeros_like(rd)
+    ddg.ddg_precondition(p, rd, zd)
+    torch.cuda.synchronize()
+    assert rel(zd.cpu().numpy(), asm.apply_lu(r)) < 1e-10
+    rep, x = ddg.ddg_fcg_solve(p, 1e-6, 500, 10)
+    _, it_ref, _ = ddm.fcg(P.A, P.b, asm.apply_lu, 1e-6, 500, 10)
+    assert rep["status"] == 0 and abs(rep["iterations"] - it_ref) <= 1
+    assert ddm.true_relative_residual(P.A, P.b, x[P.free]) < 1.2e-6
+
+
+def test_full_spmv(ddg, torch, full):
+    name, w, P, D, p = full
+    x = synth.residual_vector(P.n_free, 79)
+    xd = torch.as_tensor(x).cuda()
+    yd = torch.zeros_like(xd)
+    ddg.ddg_apply_A(p, xd, yd)
+    torch.cuda.synchronize()
+    ref = P.A @ x
+    assert np.max(np.abs(yd.cpu().numpy() - ref)) <= 1e-12 * np.abs(ref).max()
