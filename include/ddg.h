@@ -68,8 +68,10 @@ typedef struct ddg_solve_report {
     double solve_ms;           /* device time of the Krylov loop (CUDA events on the solve stream) */
     double precond_ms;         /* device time of all preconditioner applications */
     double local_ms;           /* device time of the local-solve kernel alone (GNN or band solves) */
-    int32_t local_launches;    /* launches of the local-solve kernel inside the loop */
+    int32_t local_launches;    /* kernel launches of the local solves inside the loop */
     int32_t launches;          /* all kernel launches of the library inside the loop */
+    int32_t local_applies;     /* local-solve applications (one per iteration) */
+    int32_t gnn_schedule;      /* 0: one launch per application, 1: one launch per message-passing block */
 } ddg_solve_report;
 
 /* ---- context --------------------------------------------------------- */
@@ -159,6 +161,45 @@ int32_t ddg_model_create(ddg_ctx *ctx, int32_t kbar, int32_t d, float alpha, con
                          uint64_t seed, ddg_model **out);
 int32_t ddg_model_destroy(ddg_model *m);
 int32_t ddg_model_get_weights(ddg_model *m, float *w, size_t n_w);
+
+/* Training of the DSS local solver (Section III-B, Eq. 23; optimiser of
+ * Section IV-B) on the local problems of problem p's own decomposition
+ * (Section IV-A): p is set up with DDG_DDM_LU (it stays so), preconditioned
+ * CG runs for harvest_iters - 1 iterations, and every stored residual r^n
+ * gives K samples c = R_i r^n / |R_i r^n| on the local graphs.  Each step
+ * draws `batch` samples, evaluates sum_k mean((R_i A R_i^T r_hat^k - c)^2)
+ * with hand-written forward and backward kernels, clips the gradient to
+ * global norm `clip`, and takes an Adam step (beta 0.9/0.999, eps 1e-8);
+ * the learning rate drops x0.1 after 8 windows of 50 steps without a 0.1 %
+ * improvement.  The model's weights are updated in place.  Errors:
+ * DDG_INVALID_ARG (no partition, bad options), DDG_OOM, DDG_CUDA_ERROR. */
+typedef struct ddg_train_opts {
+    int32_t steps;          /* optimiser steps */
+    int32_t batch;          /* samples per step */
+    float lr;               /* Adam learning rate (1e-2 in Section IV-B) */
+    float clip;             /* gradient-norm clip (1e-2 in Section IV-B; <= 0 disables) */
+    int32_t harvest_iters;  /* residuals kept per problem: r_0 .. r_{harvest_iters - 1} */
+    uint64_t seed;          /* SplitMix64 seed of the sample draws */
+} ddg_train_opts;
+
+typedef struct ddg_train_report {
+    int32_t samples;        /* local problems available (K x stored residuals) */
+    int32_t steps;
+    double loss_first;      /* batch loss of the first and of the last step */
+    double loss_last;
+    double ms;              /* device time of harvest and training */
+    double lr_final;
+} ddg_train_report;
+
+int32_t ddg_train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *opts, ddg_train_report *report);
+
+/* The training loss and its gradient for the given local graphs, each with
+ * c = R_i r / |R_i r| from one device residual r_dev (n_free FP64): loss =
+ * mean over graphs[0..nb) of sum_k mean((R_i A R_i^T r_hat^k - c)^2), grad =
+ * its gradient w.r.t. the flat weights (n_w floats, layout of
+ * ddg_model_create).  For checking the hand-written backward. */
+int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int32_t *graphs, int32_t nb,
+                            double *loss, float *grad);
 
 /* ---- preconditioner and solver --------------------------------------- */
 

@@ -51,7 +51,21 @@ _f64 = ctypes.c_double
 class ddg_solve_report(ctypes.Structure):
     _fields_ = [("status", _i32), ("iterations", _i32), ("rel_residual", _f64),
                 ("true_rel_residual", _f64), ("solve_ms", _f64), ("precond_ms", _f64),
-                ("local_ms", _f64), ("local_launches", _i32), ("launches", _i32)]
+                ("local_ms", _f64), ("local_launches", _i32), ("launches", _i32),
+                ("local_applies", _i32), ("gnn_schedule", _i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ddg_train_opts(ctypes.Structure):
+    _fields_ = [("steps", _i32), ("batch", _i32), ("lr", _f32), ("clip", _f32), ("harvest_iters", _i32),
+                ("seed", _u64)]
+
+
+class ddg_train_report(ctypes.Structure):
+    _fields_ = [("samples", _i32), ("steps", _i32), ("loss_first", _f64), ("loss_last", _f64), ("ms", _f64),
+                ("lr_final", _f64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +95,8 @@ _SIGS = {
     "ddg_local_corrections": [_p, _p, _p, _p, _p],
     "ddg_apply_A": [_p, _p, _p, _p],
     "ddg_apply_A_dot_noalloc": [_p, _p, _p, _p, _p],
+    "ddg_train_local_model": [_p, _p, ctypes.POINTER(ddg_train_opts), ctypes.POINTER(ddg_train_report)],
+    "ddg_train_loss_grad": [_p, _p, _p, _p, _i32, ctypes.POINTER(_f64), _p],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
 }
 for _name, _args in _SIGS.items():
@@ -301,6 +317,25 @@ def ddg_apply_A_dot_noalloc(p, x_dev, y_dev, xy_dev, stream=None) -> None:
     """y = A x and x . y into the one-element device tensor xy_dev, with no device allocation."""
     _check(lib.ddg_apply_A_dot_noalloc(p, _dev(x_dev), _dev(y_dev), _dev(xy_dev), _stream(stream, x_dev, y_dev)),
            "ddg_apply_A_dot_noalloc")
+
+
+def ddg_train_local_model(p, m, steps: int, batch: int = 32, lr: float = 1e-2, clip: float = 1e-2,
+                          harvest_iters: int = 60, seed: int = 0) -> dict:
+    """Train model m on the local problems of p's decomposition (see include/ddg.h)."""
+    o = ddg_train_opts(steps, batch, lr, clip, harvest_iters, seed)
+    rep = ddg_train_report()
+    _check(lib.ddg_train_local_model(p, m, ctypes.byref(o), ctypes.byref(rep)), "ddg_train_local_model")
+    return rep.as_dict()
+
+
+def ddg_train_loss_grad(p, m, r_dev, graphs, n_w: int):
+    """(loss, flat gradient) of the training loss for the given local graphs with residual r_dev."""
+    g_a, g_p = _host(graphs, np.int32)
+    loss = _f64()
+    grad = np.zeros(n_w, np.float32)
+    _check(lib.ddg_train_loss_grad(p, m, _dev(r_dev), g_p, g_a.size, ctypes.byref(loss), grad.ctypes.data_as(_p)),
+           "ddg_train_loss_grad")
+    return float(loss.value), grad
 
 
 def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: bool = True):

@@ -8,7 +8,6 @@
 
 namespace ddg {
 const char *last_error_cstr();
-unsigned long long launch_count();
 }
 
 using namespace ddg;
@@ -341,6 +340,26 @@ int32_t ddg_apply_A(ddg_problem *p, const double *x_dev, double *y_dev, ddg_stre
     DDG_TRY(use_device(p->ctx));
     cudaStream_t s = stream ? (cudaStream_t)stream : p->ctx->stream;
     return spmv(p, x_dev, y_dev, s);
+}
+
+int32_t ddg_train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o, ddg_train_report *report) {
+    API_BEGIN;
+    REQUIRE(p && p->assembled && p->K > 0 && m && o, "training needs an assembled, partitioned problem and a model");
+    REQUIRE(m->ctx == p->ctx, "model belongs to another context");
+    REQUIRE(o->steps >= 0 && o->batch >= 1 && o->harvest_iters >= 2 && o->lr > 0.f, "bad training options");
+    REQUIRE(p->max_loc <= DSS_MAX_NODES, "local graphs too large for the GNN kernels");
+    DDG_TRY(use_device(p->ctx));
+    int32_t st = train_local_model(p, m, o, report);
+    return st;
+}
+
+int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int32_t *graphs, int32_t nb,
+                            double *loss, float *grad) {
+    API_BEGIN;
+    REQUIRE(p && p->assembled && p->K > 0 && m && r_dev && graphs && nb >= 1 && loss, "bad arguments");
+    for (int b = 0; b < nb; ++b) REQUIRE(graphs[b] >= 0 && graphs[b] < p->K, "graph index out of range");
+    DDG_TRY(use_device(p->ctx));
+    return train_loss_grad(p, m, r_dev, graphs, nb, loss, grad);
 }
 
 int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,

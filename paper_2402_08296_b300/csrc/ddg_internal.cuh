@@ -31,6 +31,7 @@ void clear_error();
 
 // every launch site is followed by DDG_LAUNCH_CHECK (or DDG_LAUNCHES(n) for n launches)
 void note_launches(int n);
+unsigned long long launch_count();
 #define DDG_LAUNCHES(n)           \
     do {                          \
         ddg::note_launches(n);    \
@@ -184,7 +185,11 @@ int32_t dss_autotune(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
-                  ddg_solve_report *rep);
+                  ddg_solve_report *rep, double *record = nullptr);
+int32_t fcg_solve_record(ddg_problem *p, int iters, double *record, int *stored);
+int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o, ddg_train_report *rep);
+int32_t train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int *graphs_host, int nb,
+                        double *loss, float *grad_host);
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -1,0 +1,109 @@
+// Packed per-block weight layout of the GNN kernels and their shared device helpers.
+#pragma once
+
+#include "ddg_internal.cuh"
+
+namespace ddg {
+
+// ---------------------------------------------------------------- packed layout (d = 10, rows padded to 12)
+constexpr int D = DSS_D;
+constexpr int DP = 12;
+// one edge MLP
+constexpr int PHI_WA = 0;                 // [D][DP] Wa^T
+constexpr int PHI_WB = PHI_WA + D * DP;   // [D][DP] Wb^T
+constexpr int PHI_WE = PHI_WB + D * DP;   // [3][DP] We^T
+constexpr int PHI_B1 = PHI_WE + 3 * DP;   // [DP]
+constexpr int PHI_W2 = PHI_B1 + DP;       // [D][DP] W2^T
+constexpr int PHI_B2 = PHI_W2 + D * DP;   // [DP]
+constexpr int PHI_SIZE = PHI_B2 + DP;     // 420
+// block
+constexpr int OFF_OUT = 0;
+constexpr int OFF_IN = PHI_SIZE;
+constexpr int OFF_PSI = 2 * PHI_SIZE;
+constexpr int PSI_W1 = 0;                      // [3D+1][DP]
+constexpr int PSI_B1 = PSI_W1 + (3 * D + 1) * DP;
+constexpr int PSI_W2 = PSI_B1 + DP;            // [D][DP]
+constexpr int PSI_B2 = PSI_W2 + D * DP;
+constexpr int PSI_SIZE = PSI_B2 + DP;          // 516
+constexpr int OFF_DEC = OFF_PSI + PSI_SIZE;
+constexpr int DEC_W1 = 0;                      // [D][DP]
+constexpr int DEC_B1 = DEC_W1 + D * DP;
+constexpr int DEC_W2 = DEC_B1 + DP;            // [DP]
+constexpr int DEC_B2 = DEC_W2 + DP;            // [4]
+constexpr int DEC_SIZE = DEC_B2 + 4;           // 148
+constexpr int BLOCK_FLOATS = OFF_DEC + DEC_SIZE;  // 1504
+constexpr int BLOCK_BYTES = BLOCK_FLOATS * 4;     // 6016, a multiple of 16
+static_assert(BLOCK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// ---------------------------------------------------------------- bulk copy + mbarrier helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// bounded wait on a phase of an mbarrier; returns false if the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int NIN>
+__device__ __forceinline__ void mv_acc(float (&acc)[D], const float *WT, const float *x) {
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        const float4 w0 = *reinterpret_cast<const float4 *>(WT + i * DP);
+        const float4 w1 = *reinterpret_cast<const float4 *>(WT + i * DP + 4);
+        const float2 w2 = *reinterpret_cast<const float2 *>(WT + i * DP + 8);
+        const float xi = x[i];
+        acc[0] = fmaf(w0.x, xi, acc[0]);
+        acc[1] = fmaf(w0.y, xi, acc[1]);
+        acc[2] = fmaf(w0.z, xi, acc[2]);
+        acc[3] = fmaf(w0.w, xi, acc[3]);
+        acc[4] = fmaf(w1.x, xi, acc[4]);
+        acc[5] = fmaf(w1.y, xi, acc[5]);
+        acc[6] = fmaf(w1.z, xi, acc[6]);
+        acc[7] = fmaf(w1.w, xi, acc[7]);
+        acc[8] = fmaf(w2.x, xi, acc[8]);
+        acc[9] = fmaf(w2.y, xi, acc[9]);
+    }
+}
+
+__device__ __forceinline__ void load_vec(float (&v)[D], const float *src) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) v[o] = src[o];
+}
+
+// z = P_a + P_b(l) + We e  ->  S += relu(z)
+__device__ __forceinline__ void edge_msg(float (&S)[D], const float (&Pa)[D], const float *Pb, const float *We,
+                                         float ex, float ey, float en) {
+#pragma unroll
+    for (int o = 0; o < D; ++o) {
+        float z = Pa[o] + Pb[o];
+        z = fmaf(We[o], ex, z);
+        z = fmaf(We[DP + o], ey, z);
+        z = fmaf(We[2 * DP + o], en, z);
+        S[o] += fmaxf(z, 0.f);
+    }
+}
+
+}  // namespace ddg

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <vector>
 
 namespace ddg {
 
@@ -400,7 +401,7 @@ static int32_t norm2(ddg_problem *p, const double *v, double *out_dev, cudaStrea
 }
 
 int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
-                  ddg_solve_report *rep) {
+                  ddg_solve_report *rep, double *record) {
     ddg_ctx *c = p->ctx;
     cudaStream_t s = c->stream;
     const int nf = p->nf;
@@ -443,37 +444,40 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
     cudaEvent_t e0, e1;
     DDG_CU(cudaEventCreate(&e0));
     DDG_CU(cudaEventCreate(&e1));
-    // per-iteration events of one polling window: precond start/end, local kernel start/end
-    cudaEvent_t ev[POLL][4];
-    for (int q = 0; q < POLL; ++q)
-        for (int k = 0; k < 4; ++k) DDG_CU(cudaEventCreate(&ev[q][k]));
+    // per-iteration events of one polling window or captured period:
+    // precond start/end, local kernel start/end
+    const int L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
+    const int EW = std::max(POLL, L);
+    std::vector<cudaEvent_t> ev(4 * EW);
+    for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
     double pre_ms = 0.0, loc_ms = 0.0;
-    int loc_launches = 0, launches = 0, in_window = 0;
+    int loc_launches = 0, loc_applies = 0, launches = 0;
     auto drain = [&](int cnt) {
         for (int q = 0; q < cnt; ++q) {
             float a = 0.f, b = 0.f;
-            cudaEventElapsedTime(&a, ev[q][0], ev[q][1]);
-            if (p->kind != DDG_NONE) cudaEventElapsedTime(&b, ev[q][2], ev[q][3]);
+            cudaEventElapsedTime(&a, ev[4 * q], ev[4 * q + 1]);
+            if (p->kind != DDG_NONE) cudaEventElapsedTime(&b, ev[4 * q + 2], ev[4 * q + 3]);
             pre_ms += a;
             loc_ms += b;
         }
     };
-    DDG_CU(cudaEventRecord(e0, s));
     const int nb_spmv = cdiv(nf, KT);
     const long long off_sp = OFF_MD + MAXM * RB, off_rr = off_sp + 2LL * nb_spmv;
     int hflag[F_COUNT] = {0, 0, 0, 0, 0};
-    int it = 0;
-    for (; it < max_iter; ++it) {
+    // launches one FCG iteration; q indexes the iteration's event slot
+    auto launch_iter = [&](int it, int q) -> int32_t {
         Window win{};
         win.W = std::min(it, m);
         for (int j = 0; j < win.W; ++j) win.slot[j] = (it - win.W + j) % m;
         win.snew = it % m;
-        cudaEvent_t *evq = ev[in_window];
+        cudaEvent_t *evq = ev.data() + 4 * q;
         DDG_CU(cudaEventRecord(evq[0], s));
         DDG_TRY(precond_core(p, r, z, s, flag, true, p->kind != DDG_NONE ? evq + 2 : nullptr, &launches));
         DDG_CU(cudaEventRecord(evq[1], s));
-        if (p->kind != DDG_NONE) ++loc_launches;
-        ++in_window;
+        if (p->kind != DDG_NONE) {
+            ++loc_applies;
+            loc_launches += (p->kind == DDG_DDM_GNN && p->dss_sched == 1) ? p->model->kbar : 1;
+        }
         double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
         if (win.W > 0) {
             k_multidot<<<RB, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
@@ -485,14 +489,65 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
         k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
         launches += 3;
         DDG_LAUNCHES(3);
-        if (in_window == POLL || it + 1 == max_iter) {
-            DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
-            DDG_CU(cudaStreamSynchronize(s));
-            drain(in_window);
+        if (record) DDG_CU(cudaMemcpyAsync(record + (size_t)(it + 1) * nf, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+        return DDG_OK;
+    };
+    auto poll = [&](int window) -> int32_t {
+        DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+        DDG_CU(cudaStreamSynchronize(s));
+        drain(window);
+        return DDG_OK;
+    };
+    // The first m iterations grow the direction window; from iteration m on the
+    // ring slots repeat with period m, so one period is captured as a CUDA graph
+    // and replayed, polling the stop flag once per replay.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int per_launches = 0, per_loc_launches = 0, per_loc_applies = 0, per_global = 0;
+    const bool use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;
+    if (record) DDG_CU(cudaMemcpyAsync(record, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+    DDG_CU(cudaEventRecord(e0, s));
+    int it = 0, in_window = 0;
+    while (it < max_iter) {
+        if (use_graph && it >= m && it % m == 0 && max_iter - it >= L) {
+            if (!gexec) {
+                // the capture counts the period's launches once; every later replay adds them again
+                const int l0 = launches, ll0 = loc_launches, la0 = loc_applies;
+                const unsigned long long g0 = launch_count();
+                DDG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                int32_t st = DDG_OK;
+                for (int q = 0; q < L && st == DDG_OK; ++q) st = launch_iter(it + q, q);
+                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (st != DDG_OK) return st;
+                DDG_CU(ce);
+                DDG_CU(cudaGraphInstantiate(&gexec, graph, 0));
+                per_launches = launches - l0;
+                per_loc_launches = loc_launches - ll0;
+                per_loc_applies = loc_applies - la0;
+                per_global = (int)(launch_count() - g0);
+            } else {
+                launches += per_launches;
+                loc_launches += per_loc_launches;
+                loc_applies += per_loc_applies;
+                note_launches(per_global);
+            }
+            DDG_CU(cudaGraphLaunch(gexec, s));
+            it += L;
+            DDG_TRY(poll(L));
+            if (hflag[F_STOP]) break;
+            continue;
+        }
+        DDG_TRY(launch_iter(it, in_window));
+        ++it;
+        ++in_window;
+        if (in_window == POLL || it == max_iter || (use_graph && it == m)) {
+            DDG_TRY(poll(in_window));
             in_window = 0;
             if (hflag[F_STOP]) break;
         }
     }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
     DDG_CU(cudaEventRecord(e1, s));
     DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
     double hs[S_COUNT];
@@ -515,8 +570,7 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int q = 0; q < POLL; ++q)
-        for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[q][k]);
+    for (auto &e : ev) cudaEventDestroy(e);
     ddg_solve_report rp{};
     rp.iterations = hflag[F_ITERS];
     rp.rel_residual = hs[S_REL];
@@ -526,11 +580,25 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
     rp.local_ms = loc_ms;
     rp.local_launches = loc_launches;
     rp.launches = launches;
+    rp.local_applies = loc_applies;
+    rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
     rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
     if (rep) *rep = rp;
     if (rp.status == DDG_BREAKDOWN) set_error("FCG breakdown: p.q <= 0 or a non-finite scalar");
     if (rp.status == DDG_NOT_CONVERGED) set_error("FCG reached max_iter");
     return rp.status;
+}
+
+// Runs PCG (FCG with m = 1) with the current preconditioner for at most iters - 1
+// iterations and stores r_0, r_1, ... in record[iters][n_free]; returns how many
+// residuals were stored (the solve may converge earlier).
+int32_t fcg_solve_record(ddg_problem *p, int iters, double *record, int *stored) {
+    ddg_solve_report rep{};
+    int32_t st = fcg_solve(p, nullptr, 1e-14, iters - 1, 1, nullptr, &rep, record);
+    if (st != DDG_OK && st != DDG_NOT_CONVERGED && st != DDG_BREAKDOWN) return st;
+    *stored = std::min(iters, rep.iterations + 1);
+    clear_error();
+    return DDG_OK;
 }
 
 }  // namespace ddg

@@ -87,3 +87,79 @@ def test_solve_is_deterministic(ddg, ctx):
     finally:
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)
+
+
+def test_failures_are_status_codes(ddg, ctx):
+    """Host-side fault injection: every failure returns a status, none hangs or aborts."""
+    w = synth.workload("square2k", 2)
+    # HBM budget too small for the problem
+    small = ddg.ddg_create(0, 1 << 16)
+    try:
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_mesh_upload(small, w.mesh.xy, w.mesh.tri)
+        assert e.value.status == ddg.DDG_OOM
+    finally:
+        ddg.ddg_destroy(small)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    try:
+        # a part left empty by a user partition
+        part = np.zeros(ddg.ddg_problem_info(p)["n_free"], np.int32)
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_partition(p, 2, 1, part=part)
+        assert e.value.status == ddg.DDG_INVALID_ARG
+        ddg.ddg_partition(p, 4, 1)
+        # calls out of order / bad arguments
+        with pytest.raises(ddg.DdgError):
+            ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, None)
+        with pytest.raises(ddg.DdgError):
+            ddg.ddg_model_create(ctx, 30, 12, 1e-3, np.zeros(30 * (11 * 144 + 15 * 12 + 1), np.float32))
+        # non-finite weights: the Krylov loop reports a breakdown instead of iterating on NaN
+        W = synth.dss_weights(30, 10, 0)
+        W[5] = np.nan
+        m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
+        try:
+            ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+            rep, _ = ddg.ddg_fcg_solve(p, 1e-6, 50, 10)
+            assert rep["status"] == ddg.DDG_BREAKDOWN and rep["iterations"] <= 1
+        finally:
+            ddg.ddg_setup_precond(p, ddg.DDG_NONE)
+            ddg.ddg_model_destroy(m)
+        # an iteration cap is reported, not an endless loop
+        rep, _ = ddg.ddg_fcg_solve(p, 1e-12, 3, 10)
+        assert rep["status"] == ddg.DDG_NOT_CONVERGED and rep["iterations"] == 3
+    finally:
+        ddg.ddg_problem_destroy(p)
+
+
+@pytest.mark.parametrize("schedule", ["0", "1"])
+def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, schedule, monkeypatch):
+    """Both GNN schedules give the same local corrections; the CUDA-graph replay of the FCG
+    period gives the same iterates as direct launches."""
+    import torch
+    w = synth.workload("star20000", 3)
+    W = synth.dss_weights(30, 10, 3, bias_scale=0.1)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, w.K, 2)
+    m = ddg.ddg_model_create(ctx, 30, 10, 0.02, W)
+    try:
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        info = ddg.ddg_problem_info(p)
+        r = torch.as_tensor(synth.residual_vector(info["n_free"], 5)).cuda()
+        corr = torch.zeros(info["sum_k"], dtype=torch.float64, device="cuda")
+        s = torch.zeros(info["K"], dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, r, corr, s)
+        torch.cuda.synchronize()
+        if schedule == "0":
+            test_gnn_schedules_agree_and_graph_replay_matches_direct.ref = corr.cpu().numpy()
+        else:
+            ref = test_gnn_schedules_agree_and_graph_replay_matches_direct.ref
+            got = corr.cpu().numpy()
+            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+        r1, x1 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
+        monkeypatch.setenv("DDG_NO_GRAPH", "1")
+        r2, x2 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
+        assert r1["iterations"] == r2["iterations"] and np.array_equal(x1, x2)
+        assert r1["gnn_schedule"] == int(schedule)
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
