@@ -171,7 +171,9 @@ int32_t ddg_model_get_weights(ddg_model *m, float *w, size_t n_w);
  * with hand-written forward and backward kernels, clips the gradient to
  * global norm `clip`, and takes an Adam step (beta 0.9/0.999, eps 1e-8);
  * the learning rate drops x0.1 after 8 windows of 50 steps without a 0.1 %
- * improvement.  The model's weights are updated in place.  Errors:
+ * improvement.  The model's weights are updated in place; its Adam moments
+ * persist in the model, so successive calls on different problems continue
+ * one optimisation.  Errors:
  * DDG_INVALID_ARG (no partition, bad options), DDG_OOM, DDG_CUDA_ERROR. */
 typedef struct ddg_train_opts {
     int32_t steps;          /* optimiser steps */

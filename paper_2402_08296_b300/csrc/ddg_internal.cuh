@@ -77,6 +77,8 @@ struct ddg_model {
     float *packed = nullptr;  // per-block padded layout read by the GNN kernel (device)
     size_t packed_per_block = 0;
     std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
+    float *adam_m = nullptr, *adam_v = nullptr;  // Adam moments, kept across training calls
+    long long adam_t = 0;
     ddg::Allocs allocs;
 };
 

@@ -640,11 +640,16 @@ struct Trainer {
         const long long nw = (long long)m->kbar * per_block;
         DDG_TRY(ws.get(&gpack, (size_t)m->kbar * BLOCK_FLOATS));
         DDG_TRY(ws.get(&gflat, nw));
-        DDG_TRY(ws.get(&m1, nw));
-        DDG_TRY(ws.get(&m2, nw));
         DDG_TRY(ws.get(&stats, 4));
-        DDG_CU(cudaMemsetAsync(m1, 0, sizeof(float) * nw, s));
-        DDG_CU(cudaMemsetAsync(m2, 0, sizeof(float) * nw, s));
+        if (!m->adam_m) {
+            DDG_TRY(dalloc(m->ctx, m->allocs, &m->adam_m, nw));
+            DDG_TRY(dalloc(m->ctx, m->allocs, &m->adam_v, nw));
+            DDG_CU(cudaMemsetAsync(m->adam_m, 0, sizeof(float) * nw, s));
+            DDG_CU(cudaMemsetAsync(m->adam_v, 0, sizeof(float) * nw, s));
+            m->adam_t = 0;
+        }
+        m1 = m->adam_m;
+        m2 = m->adam_v;
         return DDG_OK;
     }
 
@@ -787,7 +792,7 @@ int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o,
         }
         double loss = 0.0;
         DDG_TRY(tr.loss_grad(graphs, res, &loss));
-        DDG_TRY(tr.adam_step(step, (float)lr, o->clip));
+        DDG_TRY(tr.adam_step((int)(++m->adam_t), (float)lr, o->clip));
         if (first < 0.0) first = loss;
         last = loss;
         window += loss;

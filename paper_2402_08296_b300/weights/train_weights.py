@@ -1,0 +1,87 @@
+"""Prepare the DSS weights of the benchmark with the library's own training kernels.
+
+Recipe of Section IV-A/IV-B: random star-shaped domains (seeds disjoint from the
+benchmark's and the tests'), each decomposed into ~1000-node subdomains with
+two overlap layers; ``ddg_train_local_model`` harvests the residuals of
+DDM-LU preconditioned CG on the domain and trains the model on the resulting
+local problems (Adam, lr 1e-2, gradient-norm clip 1e-2, plateau decay).  The
+Adam state lives in the model, so the meshes form one optimisation; the
+learning rate drops x0.1 when the mean loss of a round over all meshes stops
+improving.
+
+Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15
+Writes dss_k30_d10.npy (flat float32 weights, layout of include/ddg.h).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import paper_2402_08296_b300 as ddg  # noqa: E402
+import synth  # noqa: E402
+
+KBAR, D, ALPHA = 30, 10, 1e-3
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--minutes", type=float, default=15.0)
+    ap.add_argument("--meshes", type=int, default=8)
+    ap.add_argument("--nodes", type=int, default=30000)
+    ap.add_argument("--steps", type=int, default=200, help="optimiser steps per mesh and round")
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--harvest", type=int, default=60)
+    ap.add_argument("--out", default=os.path.join(HERE, "dss_k30_d10.npy"))
+    ap.add_argument("--log", default=None)
+    a = ap.parse_args()
+    log = open(a.log, "w") if a.log else sys.stdout
+    ctx = ddg.ddg_create(0)
+    model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, None, seed=2024)
+    problems = []
+    for s in range(a.meshes):
+        seed = 5000 + s
+        m = synth.star_mesh(a.nodes, seed=seed)
+        K = max(1, int(round((m.n - m.n_boundary_ring) / 1000.0)))
+        p = ddg.ddg_mesh_upload(ctx, m.xy, m.tri)
+        ddg.ddg_assemble_poly(p, synth.poly_coeffs(seed))
+        ddg.ddg_partition(p, K, 2)
+        problems.append(p)
+    lr, best, stale, rnd = 1e-2, np.inf, 0, 0
+    t0 = time.time()
+    n_w = KBAR * synth.n_weights_per_block(D)
+    while time.time() - t0 < 60.0 * a.minutes:
+        losses = []
+        for i, p in enumerate(problems):
+            rep = ddg.ddg_train_local_model(p, model, steps=a.steps, batch=a.batch, lr=lr, clip=1e-2,
+                                            harvest_iters=a.harvest, seed=1000 * rnd + i)
+            losses.append(rep["loss_last"])
+            print(f"round {rnd} mesh {i} samples {rep['samples']} loss {rep['loss_first']:.3e} -> "
+                  f"{rep['loss_last']:.3e} lr {lr:.1e} {rep['ms'] / 1e3:.1f}s t {time.time() - t0:.0f}s",
+                  file=log, flush=True)
+            if time.time() - t0 > 60.0 * a.minutes:
+                break
+        mean = float(np.mean(losses))
+        if mean < 0.99 * best:
+            best, stale = mean, 0
+        else:
+            stale += 1
+            if stale >= 2:
+                lr, stale = lr * 0.1, 0
+        rnd += 1
+    np.save(a.out, ddg.ddg_model_get_weights(model, n_w))
+    print(f"saved {a.out} after {rnd} rounds", file=log, flush=True)
+    for p in problems:
+        ddg.ddg_problem_destroy(p)
+    ddg.ddg_model_destroy(model)
+    ddg.ddg_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()
