@@ -119,6 +119,7 @@ int32_t ddg_problem_destroy(ddg_problem *p) {
     cudaStreamSynchronize(c->stream);
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
+    chunk_free(p);
     dfree_all(c, p->a_part);
     dfree_all(c, p->a_matrix);
     dfree_all(c, p->a_mesh);
@@ -296,6 +297,7 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
     dfree_all(c, p->a_kry);
     p->kr_m = 0;
     dfree_all(c, p->a_pre);
+    chunk_free(p);
     p->kind = DDG_NONE;
     p->flags = flags;
     p->model = model;
@@ -309,6 +311,7 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
     } else {
         DDG_TRY(dss_check_capacity(p));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_D * p->sum_loc));
+        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, (size_t)DSS_D * p->sum_loc));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_c, p->sum_loc));
         p->kind = kind;
         DDG_TRY(dss_autotune(p));

@@ -66,6 +66,12 @@ struct ddg_ctx {
     cudaStream_t stream = nullptr;
     size_t budget = 0;
     size_t in_use = 0;
+    // GNN schedule chosen by the autotuner, cached per decomposition shape (K, graph nodes, largest graph)
+    struct Tuned {
+        long long K, nodes, max_loc;
+        int sched, T;
+    };
+    std::vector<Tuned> tuned;
 };
 
 struct ddg_model {
@@ -79,6 +85,15 @@ struct ddg_model {
     std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
     float *adam_m = nullptr, *adam_v = nullptr;  // Adam moments, kept across training calls
     long long adam_t = 0;
+    ddg::Allocs allocs;
+};
+
+// chunked GNN schedule: graphs cut into chunks of at most 2 * T nodes (see dss.cu)
+struct ChunkPlan {
+    int T = 0, nchunks = 0, max_need = 0;
+    int *c_graph = nullptr, *c_n0 = nullptr, *c_own = nullptr, *c_need_off = nullptr, *c_need_n = nullptr;
+    int *need = nullptr, *c_adj_off = nullptr, *adj_ptr = nullptr, *c_adj_base = nullptr;
+    uint16_t *adj = nullptr;
     ddg::Allocs allocs;
 };
 
@@ -141,8 +156,10 @@ struct ddg_problem {
     double *lu_band = nullptr;
     int lu_kmax = 0;
     double *s = nullptr, *y = nullptr, *wc = nullptr, *corr = nullptr;
-    int dss_sched = 0;          // GNN schedule: 0 = one persistent launch, 1 = one launch per block
-    float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedule 1)
+    int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block
+    float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedules 1, 2)
+    float *dss_h2 = nullptr;    // second latent buffer (schedule 2)
+    ChunkPlan chunk;
     ddg::Allocs a_pre;
 
     // Krylov workspace (stage "krylov")
@@ -184,6 +201,8 @@ int32_t model_pack(ddg_model *m);
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
+int32_t chunk_build(ddg_problem *p, int T);
+void chunk_free(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,

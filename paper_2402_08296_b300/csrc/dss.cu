@@ -17,6 +17,8 @@
 // into the other half of a double buffer while the current block computes.
 #include "dss_layout.cuh"
 
+#include <climits>
+
 #include <cmath>
 
 namespace ddg {
@@ -516,6 +518,397 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss_step(const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------- chunked per-block schedule
+// Each graph is cut into chunks of at most 2 * T consecutive local nodes; a CTA
+// of T threads owns one chunk.  Its shared memory holds the neighbour
+// projections of the chunk's nodes and of their neighbours only, addressed by
+// chunk-local ids built at set-up, so several CTAs share an SM and every SM
+// receives work even when there are fewer graphs than SMs.  Latents alternate
+// between two global buffers, because a chunk reads the latents of nodes that
+// other chunks update in the same launch.
+struct ChunkArgs {
+    const int *c_graph, *c_n0, *c_own;      // per chunk: graph, first own node (graph-local), own count
+    const int *c_need_off, *c_need_n;       // per chunk: start / count of its needed-node list
+    const int *need;                        // graph-local ids: own nodes first, then outside neighbours
+    const int *c_adj_off;                   // per chunk: start of its own nodes' CSR in adj_ptr
+    const int *adj_ptr;                     // own-node CSR offsets (relative to the chunk's adj start)
+    const uint16_t *adj;                    // chunk-local neighbour ids
+    const int *c_adj_base;                  // per chunk: start of its slice in adj
+    const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
+    const float2 *loc_xy;
+    const double *r, *s;
+    double *corr;
+    const float *h_in;                      // [D][n_total]
+    float *h_out;                           // [D][n_total]
+    float *c;                               // [n_total]
+    long long n_total;
+    float alpha;
+    int first, last;
+    const int *stop;
+};
+
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid_constant__ BlockWeights W,
+                                                 const __grid_constant__ ChunkArgs a) {
+    extern __shared__ __align__(16) float Pb[];  // [needed][2 D]
+    if (a.stop && *a.stop) return;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const int g = a.c_graph[q];
+    const int lp = a.loc_ptr[g];
+    const int k = a.loc_nint[g];
+    const int s0 = a.sub_ptr[g];
+    const double s = a.s[g];
+    const int n0 = a.c_n0[q], own = a.c_own[q];
+    const int nn = a.c_need_n[q];
+    const int *need = a.need + a.c_need_off[q];
+    if (s == 0.0) {
+        if (a.last)
+            for (int t = tid; t < own; t += T)
+                if (n0 + t < k) a.corr[s0 + n0 + t] = 0.0;
+        return;
+    }
+    // phase A: projections of every needed node
+    for (int u = tid; u < nn; u += T) {
+        const int j = need[u];
+        float h[D], po[D], pi[D];
+        if (a.first) {
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = 0.f;
+        } else {
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = a.h_in[o * a.n_total + lp + j];
+        }
+#pragma unroll
+        for (int o = 0; o < D; ++o) { po[o] = 0.f; pi[o] = 0.f; }
+        mvc_acc<D, OFF_OUT + PHI_WB>(po, W, h);
+        mvc_acc<D, OFF_IN + PHI_WB>(pi, W, h);
+        float4 *dst = reinterpret_cast<float4 *>(Pb + (size_t)u * 2 * D);
+        dst[0] = make_float4(po[0], po[1], po[2], po[3]);
+        dst[1] = make_float4(po[4], po[5], po[6], po[7]);
+        dst[2] = make_float4(po[8], po[9], pi[0], pi[1]);
+        dst[3] = make_float4(pi[2], pi[3], pi[4], pi[5]);
+        dst[4] = make_float4(pi[6], pi[7], pi[8], pi[9]);
+    }
+    __syncthreads();
+    const int *aptr = a.adj_ptr + a.c_adj_off[q];
+    const uint16_t *adj = a.adj + a.c_adj_base[q];
+    const float2 *xy = a.loc_xy + lp;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int u = p * T + tid;  // chunk-local id of an own node
+        if (u >= own) continue;
+        const int j = n0 + u;       // graph-local id
+        const bool inner = j < k;
+        float h[D], c;
+        if (a.first) {
+            c = inner ? (float)(a.r[a.sub_idx[s0 + j]] / s) : 0.f;
+            a.c[lp + j] = c;
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = 0.f;
+        } else {
+            c = a.c[lp + j];
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = a.h_in[o * a.n_total + lp + j];
+        }
+        const float2 xj = xy[j];
+        float Pa_o[D], Pa_i[D], So[D], Si[D];
+        loadc<OFF_OUT + PHI_B1>(Pa_o, W);
+        loadc<OFF_IN + PHI_B1>(Pa_i, W);
+        mvc_acc<D, OFF_OUT + PHI_WA>(Pa_o, W, h);
+        mvc_acc<D, OFF_IN + PHI_WA>(Pa_i, W, h);
+#pragma unroll
+        for (int o = 0; o < D; ++o) { So[o] = 0.f; Si[o] = 0.f; }
+        int dout = 0, din = 0;
+        for (int e = aptr[u]; e < aptr[u + 1]; ++e) {
+            const int v = adj[e];          // chunk-local
+            const int l = need[v];         // graph-local
+            const float2 xl = xy[l];
+            const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+            const float dn = sqrtf(dx * dx + dy * dy);
+            const float *pbl = Pb + (size_t)v * 2 * D;
+            if (l < k) {
+                edge_msg_c<OFF_OUT + PHI_WE>(So, Pa_o, pbl, W, dx, dy, dn);
+                ++dout;
+            }
+            if (inner) {
+                edge_msg_c<OFF_IN + PHI_WE>(Si, Pa_i, pbl + D, W, -dx, -dy, dn);
+                ++din;
+            }
+        }
+        float phi_o[D], phi_i[D];
+        const float fo = (float)dout, fi = (float)din;
+#pragma unroll
+        for (int o = 0; o < D; ++o) {
+            phi_o[o] = fo * W.w[OFF_OUT + PHI_B2 + o];
+            phi_i[o] = fi * W.w[OFF_IN + PHI_B2 + o];
+        }
+        mvc_acc<D, OFF_OUT + PHI_W2>(phi_o, W, So);
+        mvc_acc<D, OFF_IN + PHI_W2>(phi_i, W, Si);
+        float hid[D];
+        loadc<OFF_PSI + PSI_B1>(hid, W);
+        mvc_acc<D, OFF_PSI + PSI_W1>(hid, W, h);
+        {
+            float cc[1] = {c};
+            mvc_acc<1, OFF_PSI + PSI_W1 + D * DP>(hid, W, cc);
+        }
+        mvc_acc<D, OFF_PSI + PSI_W1 + (D + 1) * DP>(hid, W, phi_o);
+        mvc_acc<D, OFF_PSI + PSI_W1 + (2 * D + 1) * DP>(hid, W, phi_i);
+#pragma unroll
+        for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+        float out[D];
+        loadc<OFF_PSI + PSI_B2>(out, W);
+        mvc_acc<D, OFF_PSI + PSI_W2>(out, W, hid);
+#pragma unroll
+        for (int o = 0; o < D; ++o) h[o] = fmaf(a.alpha, out[o], h[o]);
+        if (a.last) {
+            if (inner) {
+                float dh[D];
+                loadc<OFF_DEC + DEC_B1>(dh, W);
+                mvc_acc<D, OFF_DEC + DEC_W1>(dh, W, h);
+                float y = W.w[OFF_DEC + DEC_B2];
+#pragma unroll
+                for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], fmaxf(dh[o], 0.f), y);
+                a.corr[s0 + j] = s * (double)y;
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < D; ++o) a.h_out[o * a.n_total + lp + j] = h[o];
+        }
+    }
+}
+
+// set-up of the chunks of one graph per CTA: needed-node lists and chunk-local adjacency.
+// Pass 0 counts (needed nodes, adjacency entries) per chunk; pass 1 fills.
+constexpr int CH_T = 256;
+constexpr int CH_MAX_NEED = 2048;
+
+__global__ void __launch_bounds__(CH_T) k_chunk_build(const int *c_graph, const int *c_n0, const int *c_own,
+                                                      const int *loc_ptr, const int *nbr_ptr, const int *nbr_off,
+                                                      const uint16_t *nbr, int pass, int *need_n, int *adj_n,
+                                                      const int *need_off, int *need, const int *adj_off,
+                                                      int *adj_ptr, const int *adj_base, uint16_t *adj, int *st) {
+    __shared__ int cand[CH_MAX_NEED];
+    __shared__ int cnt;
+    const int q = blockIdx.x;
+    const int g = c_graph[q], n0 = c_n0[q], own = c_own[q];
+    const int lp = loc_ptr[g];
+    const int *gptr = nbr_ptr + lp + g;
+    const uint16_t *gn = nbr + nbr_off[g];
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < own; t += CH_T) {
+        const int j = n0 + t;
+        for (int e = gptr[j]; e < gptr[j + 1]; ++e) {
+            const int l = gn[e];
+            if (l < n0 || l >= n0 + own) {
+                int pos = atomicAdd(&cnt, 1);
+                if (pos < CH_MAX_NEED) cand[pos] = l;
+            }
+        }
+    }
+    __syncthreads();
+    const int m = cnt;
+    if (m > CH_MAX_NEED) {
+        if (threadIdx.x == 0) raise_status(st, ST_TOO_LARGE);
+        return;
+    }
+    int N = 1;
+    while (N < m) N <<= 1;
+    for (int t = m + threadIdx.x; t < N; t += CH_T) cand[t] = INT_MAX;
+    __syncthreads();
+    for (int kk = 2; kk <= N; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < N; t += CH_T) {
+                int r = t ^ j;
+                if (r > t) {
+                    bool up = (t & kk) == 0;
+                    int x = cand[t], y = cand[r];
+                    if ((x > y) == up) { cand[t] = y; cand[r] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __shared__ int uniq;
+    if (threadIdx.x == 0) {
+        int u = 0;
+        for (int t = 0; t < m; ++t)
+            if (t == 0 || cand[t] != cand[t - 1]) cand[u++] = cand[t];
+        uniq = u;
+    }
+    __syncthreads();
+    const int ext = uniq;
+    if (pass == 0) {
+        if (threadIdx.x == 0) {
+            need_n[q] = own + ext;
+            adj_n[q] = gptr[n0 + own] - gptr[n0];
+        }
+        return;
+    }
+    int *nd = need + need_off[q];
+    for (int t = threadIdx.x; t < own; t += CH_T) nd[t] = n0 + t;
+    for (int t = threadIdx.x; t < ext; t += CH_T) nd[own + t] = cand[t];
+    int *ap = adj_ptr + adj_off[q];
+    uint16_t *ad = adj + adj_base[q];
+    const int e00 = gptr[n0];
+    for (int t = threadIdx.x; t <= own; t += CH_T) ap[t] = gptr[n0 + t] - e00;
+    for (int t = threadIdx.x; t < own; t += CH_T) {
+        const int j = n0 + t;
+        for (int e = gptr[j]; e < gptr[j + 1]; ++e) {
+            const int l = gn[e];
+            int v;
+            if (l >= n0 && l < n0 + own) {
+                v = l - n0;
+            } else {
+                int lo = 0, hi = ext;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (cand[mid] < l) lo = mid + 1; else hi = mid;
+                }
+                v = own + lo;
+            }
+            ad[e - e00] = (uint16_t)v;
+        }
+    }
+}
+
+void chunk_free(ddg_problem *p) {
+    dfree_all(p->ctx, p->chunk.allocs);
+    ChunkPlan empty;
+    p->chunk.T = p->chunk.nchunks = p->chunk.max_need = 0;
+    p->chunk.c_graph = p->chunk.c_n0 = p->chunk.c_own = p->chunk.c_need_off = p->chunk.c_need_n = nullptr;
+    p->chunk.need = p->chunk.c_adj_off = p->chunk.adj_ptr = p->chunk.c_adj_base = nullptr;
+    p->chunk.adj = nullptr;
+    (void)empty;
+}
+
+int32_t chunk_build(ddg_problem *p, int T) {
+    ddg_ctx *c = p->ctx;
+    cudaStream_t s = c->stream;
+    chunk_free(p);
+    ChunkPlan &cp = p->chunk;
+    const int K = p->K;
+    std::vector<int> lp(K + 1);
+    DDG_CU(cudaMemcpyAsync(lp.data(), p->loc_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    std::vector<int> cg, cn0, cown;
+    for (int g = 0; g < K; ++g) {
+        const int nl = lp[g + 1] - lp[g];
+        const int nq = std::max(1, cdiv(nl, 2 * T));
+        const int cs = cdiv(nl, nq);
+        for (int q = 0; q < nq; ++q) {
+            cg.push_back(g);
+            cn0.push_back(q * cs);
+            cown.push_back(std::min(cs, nl - q * cs));
+        }
+    }
+    const int nc = (int)cg.size();
+    cp.T = T;
+    cp.nchunks = nc;
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_graph, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_n0, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_own, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_off, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_n, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_off, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_base, nc));
+    DDG_CU(cudaMemcpyAsync(cp.c_graph, cg.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    int *adj_n = nullptr;
+    DDG_CU(cudaMallocAsync(&adj_n, sizeof(int) * nc, s));
+    k_chunk_build<<<nc, CH_T, 0, s>>>(cp.c_graph, cp.c_n0, cp.c_own, p->loc_ptr, p->nbr_ptr, p->nbr_off, p->nbr, 0,
+                                      cp.c_need_n, adj_n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      p->d_status);
+    DDG_LAUNCH_CHECK();
+    std::vector<int> hn(nc), ha(nc);
+    DDG_CU(cudaMemcpyAsync(hn.data(), cp.c_need_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaMemcpyAsync(ha.data(), adj_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    DDG_TRY(check_status(p, "GNN chunks"));
+    std::vector<int> noff(nc), aoff(nc), abase(nc);
+    long long tn = 0, ta = 0, tp = 0;
+    int maxn = 0;
+    for (int q = 0; q < nc; ++q) {
+        noff[q] = (int)tn;
+        abase[q] = (int)ta;
+        aoff[q] = (int)tp;
+        tn += hn[q];
+        ta += ha[q];
+        tp += cown[q] + 1;
+        maxn = std::max(maxn, hn[q]);
+    }
+    cp.max_need = maxn;
+    DDG_TRY(dalloc(c, cp.allocs, &cp.need, tn));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.adj, ta));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.adj_ptr, tp));
+    DDG_CU(cudaMemcpyAsync(cp.c_need_off, noff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_adj_off, aoff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_adj_base, abase.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    k_chunk_build<<<nc, CH_T, 0, s>>>(cp.c_graph, cp.c_n0, cp.c_own, p->loc_ptr, p->nbr_ptr, p->nbr_off, p->nbr, 1,
+                                      nullptr, nullptr, cp.c_need_off, cp.need, cp.c_adj_off, cp.adj_ptr,
+                                      cp.c_adj_base, cp.adj, p->d_status);
+    DDG_LAUNCH_CHECK();
+    DDG_CU(cudaFreeAsync(adj_n, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    return check_status(p, "GNN chunks");
+}
+
+template <int T>
+static int32_t launch_chunks(ddg_problem *p, const ChunkArgs &base, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss_chunk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        configured = true;
+    }
+    const ddg_model *m = p->model;
+    const size_t smem = (size_t)p->chunk.max_need * 2 * D * sizeof(float);
+    for (int blk = 0; blk < m->kbar; ++blk) {
+        ChunkArgs a = base;
+        a.first = blk == 0;
+        a.last = blk == m->kbar - 1;
+        a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
+        a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
+        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(m->packed_host.data()) + blk;
+        k_dss_chunk<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
+    }
+    DDG_LAUNCHES(m->kbar);
+    return DDG_OK;
+}
+
+int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+    const ChunkPlan &cp = p->chunk;
+    ChunkArgs a{};
+    a.c_graph = cp.c_graph;
+    a.c_n0 = cp.c_n0;
+    a.c_own = cp.c_own;
+    a.c_need_off = cp.c_need_off;
+    a.c_need_n = cp.c_need_n;
+    a.need = cp.need;
+    a.c_adj_off = cp.c_adj_off;
+    a.adj_ptr = cp.adj_ptr;
+    a.adj = cp.adj;
+    a.c_adj_base = cp.c_adj_base;
+    a.loc_ptr = p->loc_ptr;
+    a.loc_nint = p->loc_nint;
+    a.sub_ptr = p->sub_ptr;
+    a.sub_idx = p->sub_idx;
+    a.loc_xy = p->loc_xy;
+    a.r = r;
+    a.s = p->s;
+    a.corr = p->corr;
+    a.c = p->dss_c;
+    a.n_total = p->sum_loc;
+    a.alpha = p->model->alpha;
+    a.stop = stop;
+    switch (cp.T) {
+        case 128: return launch_chunks<128>(p, a, s);
+        case 192: return launch_chunks<192>(p, a, s);
+        case 256: return launch_chunks<256>(p, a, s);
+        default: set_error("no chunk plan"); return DDG_INVALID_ARG;
+    }
+}
+
 static size_t dss_smem_bytes(int nmax, int emax) {
     size_t b = 128 + 2 * (size_t)BLOCK_BYTES;
     b += (size_t)nmax * 2 * D * sizeof(float);
@@ -588,6 +981,7 @@ int32_t dss_step_launch(ddg_problem *p, const double *r, const int *stop, cudaSt
 
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     if (p->dss_sched == 1) return dss_step_launch(p, r, stop, s);
+    if (p->dss_sched == 2) return dss_chunk_launch(p, r, stop, s);
     const ddg_model *m = p->model;
     DssArgs a;
     a.weights = m->packed;

@@ -126,6 +126,16 @@ __global__ void k_copy(const double *a, double *b, int n, const int *stop) {
     if (i < n) b[i] = a[i];
 }
 
+// records an event; inside a stream capture it becomes an event-record node that
+// records each time the graph runs (a plain record would only be a dependency)
+static cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess) return err;
+    return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                                : cudaEventRecordDefault);
+}
+
 // launches the preconditioner's kernels; ev_local (optional) brackets the local-solve kernel;
 // *launches (optional) is increased by the number of kernels launched
 static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStream_t s, const int *stop,
@@ -150,13 +160,13 @@ static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStre
         DDG_LAUNCH_CHECK();
         ++nl;
     }
-    if (ev_local) DDG_CU(cudaEventRecord(ev_local[0], s));
+    if (ev_local) DDG_CU(record_event(ev_local[0], s));
     if (p->kind == DDG_DDM_GNN) {
         DDG_TRY(dss_launch_args(p, r, stop, s));
     } else {
         DDG_TRY(lu_apply_launch(p, r, stop, s));
     }
-    if (ev_local) DDG_CU(cudaEventRecord(ev_local[1], s));
+    if (ev_local) DDG_CU(record_event(ev_local[1], s));
     ++nl;
     if (prolong) {
         k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->mult, p->corr, p->wc,
@@ -179,23 +189,37 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
     return DDG_OK;
 }
 
-// Picks the faster GNN schedule for this decomposition (one persistent launch,
-// or one launch per block with the weights in the constant bank) by timing
-// both on the right-hand side; DDG_GNN_SCHEDULE=0/1 in the environment forces one.
+// Picks the fastest GNN schedule for this decomposition by timing each on the
+// right-hand side: 0 = one persistent launch per application; 1 = one launch
+// per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
+// the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256).
+// DDG_GNN_SCHEDULE = 0, 1, 2 (and DDG_GNN_CHUNK_T = 128/192/256) forces one.
+// The choice is cached in the context per decomposition shape.
 int32_t dss_autotune(ddg_problem *p) {
     const char *env = getenv("DDG_GNN_SCHEDULE");
-    if (env && (env[0] == '0' || env[0] == '1')) {
+    const char *envT = getenv("DDG_GNN_CHUNK_T");
+    if (env && (env[0] == '0' || env[0] == '1' || env[0] == '2')) {
         p->dss_sched = env[0] - '0';
+        if (p->dss_sched == 2) DDG_TRY(chunk_build(p, envT ? atoi(envT) : 192));
         return DDG_OK;
+    }
+    for (const auto &t : p->ctx->tuned) {
+        if (t.K == p->K && t.nodes == p->sum_loc && t.max_loc == p->max_loc) {
+            p->dss_sched = t.sched;
+            if (t.sched == 2) DDG_TRY(chunk_build(p, t.T));
+            return DDG_OK;
+        }
     }
     cudaStream_t s = p->ctx->stream;
     cudaEvent_t e0, e1;
     DDG_CU(cudaEventCreate(&e0));
     DDG_CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int pick = 0;
-    for (int sched = 0; sched < 2; ++sched) {
-        p->dss_sched = sched;
+    int pick = 0, pickT = 0;
+    const int cands[5][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}};
+    for (const auto &cd : cands) {
+        p->dss_sched = cd[0];
+        if (cd[0] == 2) DDG_TRY(chunk_build(p, cd[1]));
         DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
         DDG_CU(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 2; ++rep) DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
@@ -205,12 +229,19 @@ int32_t dss_autotune(ddg_problem *p) {
         DDG_CU(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
-            pick = sched;
+            pick = cd[0];
+            pickT = cd[1];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->dss_sched = pick;
+    if (pick == 2) {
+        if (p->chunk.T != pickT) DDG_TRY(chunk_build(p, pickT));
+    } else {
+        chunk_free(p);
+    }
+    p->ctx->tuned.push_back({(long long)p->K, p->sum_loc, (long long)p->max_loc, pick, pickT});
     return check_status(p, "GNN schedule selection");
 }
 
@@ -455,8 +486,9 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
     auto drain = [&](int cnt) {
         for (int q = 0; q < cnt; ++q) {
             float a = 0.f, b = 0.f;
-            cudaEventElapsedTime(&a, ev[4 * q], ev[4 * q + 1]);
-            if (p->kind != DDG_NONE) cudaEventElapsedTime(&b, ev[4 * q + 2], ev[4 * q + 3]);
+            if (cudaEventElapsedTime(&a, ev[4 * q], ev[4 * q + 1]) != cudaSuccess) a = 0.f;
+            if (p->kind != DDG_NONE && cudaEventElapsedTime(&b, ev[4 * q + 2], ev[4 * q + 3]) != cudaSuccess) b = 0.f;
+            cudaGetLastError();
             pre_ms += a;
             loc_ms += b;
         }
@@ -471,9 +503,9 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
         for (int j = 0; j < win.W; ++j) win.slot[j] = (it - win.W + j) % m;
         win.snew = it % m;
         cudaEvent_t *evq = ev.data() + 4 * q;
-        DDG_CU(cudaEventRecord(evq[0], s));
+        DDG_CU(record_event(evq[0], s));
         DDG_TRY(precond_core(p, r, z, s, flag, true, p->kind != DDG_NONE ? evq + 2 : nullptr, &launches));
-        DDG_CU(cudaEventRecord(evq[1], s));
+        DDG_CU(record_event(evq[1], s));
         if (p->kind != DDG_NONE) {
             ++loc_applies;
             loc_launches += (p->kind == DDG_DDM_GNN && p->dss_sched == 1) ? p->model->kbar : 1;

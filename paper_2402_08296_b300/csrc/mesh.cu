@@ -323,6 +323,7 @@ int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal_host, c
     cudaStream_t s = c->stream;
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
+    chunk_free(p);
     dfree_all(c, p->a_part);
     dfree_all(c, p->a_matrix);
     p->assembled = false;

@@ -595,6 +595,7 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     cudaStream_t s = c->stream;
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
+    chunk_free(p);
     dfree_all(c, p->a_part);
     p->kind = DDG_NONE;
     p->K = 0;
