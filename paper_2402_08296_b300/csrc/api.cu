@@ -90,6 +90,7 @@ int32_t ddg_mesh_upload(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n
     DDG_TRY(use_device(c));
     ddg_problem *p = new ddg_problem();
     p->ctx = c;
+    p->stream = c->stream;
     p->n = n_nodes;
     p->t = n_tri;
     int32_t st = DDG_OK;
@@ -97,9 +98,9 @@ int32_t ddg_mesh_upload(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n
         if ((st = dalloc(c, p->a_mesh, &p->d_status, 1)) != DDG_OK) break;
         if ((st = dalloc(c, p->a_mesh, &p->xy, 2LL * n_nodes)) != DDG_OK) break;
         if ((st = dalloc(c, p->a_mesh, &p->tri, 3LL * n_tri)) != DDG_OK) break;
-        cudaMemsetAsync(p->d_status, 0, sizeof(int), c->stream);
-        cudaMemcpyAsync(p->xy, xy, sizeof(double) * 2 * n_nodes, cudaMemcpyHostToDevice, c->stream);
-        cudaMemcpyAsync(p->tri, tri, sizeof(int) * 3 * n_tri, cudaMemcpyHostToDevice, c->stream);
+        cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream);
+        cudaMemcpyAsync(p->xy, xy, sizeof(double) * 2 * n_nodes, cudaMemcpyHostToDevice, p->stream);
+        cudaMemcpyAsync(p->tri, tri, sizeof(int) * 3 * n_tri, cudaMemcpyHostToDevice, p->stream);
         st = mesh_build(p, dirichlet);
     } while (0);
     if (st != DDG_OK) {
@@ -116,13 +117,14 @@ int32_t ddg_problem_destroy(ddg_problem *p) {
     if (!p) return DDG_OK;
     ddg_ctx *c = p->ctx;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(p->stream);
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
     chunk_free(p);
     dfree_all(c, p->a_part);
     dfree_all(c, p->a_matrix);
     dfree_all(c, p->a_mesh);
+    if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
     return DDG_OK;
 }
@@ -164,7 +166,7 @@ int32_t ddg_matrix_download(ddg_problem *p, int32_t *rowptr, int32_t *col, doubl
     API_BEGIN;
     REQUIRE(p && p->assembled, "problem not assembled");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     if (rowptr) DDG_CU(cudaMemcpyAsync(rowptr, p->rowptr, sizeof(int) * (p->nf + 1), cudaMemcpyDeviceToHost, s));
     if (col) DDG_CU(cudaMemcpyAsync(col, p->col, sizeof(int) * p->nnz, cudaMemcpyDeviceToHost, s));
     if (val) DDG_CU(cudaMemcpyAsync(val, p->val, sizeof(double) * p->nnz, cudaMemcpyDeviceToHost, s));
@@ -187,7 +189,7 @@ int32_t ddg_partition_download(ddg_problem *p, int32_t *part, int32_t *sub_ptr, 
     API_BEGIN;
     REQUIRE(p && p->K > 0, "no partition");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     if (part) DDG_CU(cudaMemcpyAsync(part, p->part, sizeof(int) * p->nf, cudaMemcpyDeviceToHost, s));
     if (sub_ptr) DDG_CU(cudaMemcpyAsync(sub_ptr, p->sub_ptr, sizeof(int) * (p->K + 1), cudaMemcpyDeviceToHost, s));
     if (sub_idx) DDG_CU(cudaMemcpyAsync(sub_idx, p->sub_idx, sizeof(int) * p->sum_k, cudaMemcpyDeviceToHost, s));
@@ -201,7 +203,7 @@ int32_t ddg_graph_download(ddg_problem *p, int32_t *loc_ptr, int32_t *n_int, int
     API_BEGIN;
     REQUIRE(p && p->K > 0, "no partition");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     if (loc_ptr) DDG_CU(cudaMemcpyAsync(loc_ptr, p->loc_ptr, sizeof(int) * (p->K + 1), cudaMemcpyDeviceToHost, s));
     if (n_int) DDG_CU(cudaMemcpyAsync(n_int, p->loc_nint, sizeof(int) * p->K, cudaMemcpyDeviceToHost, s));
     if (loc_node) DDG_CU(cudaMemcpyAsync(loc_node, p->loc_node, sizeof(int) * p->sum_loc, cudaMemcpyDeviceToHost, s));
@@ -221,7 +223,7 @@ int32_t ddg_coarse_download(ddg_problem *p, double *A0, double *A0_inv) {
     API_BEGIN;
     REQUIRE(p && p->K > 0, "no partition");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     size_t bytes = sizeof(double) * p->K * p->K;
     if (A0) DDG_CU(cudaMemcpyAsync(A0, p->A0, bytes, cudaMemcpyDeviceToHost, s));
     if (A0_inv) DDG_CU(cudaMemcpyAsync(A0_inv, p->A0inv, bytes, cudaMemcpyDeviceToHost, s));
@@ -324,7 +326,7 @@ int32_t ddg_precondition(ddg_problem *p, const double *r_dev, double *z_dev, ddg
     API_BEGIN;
     REQUIRE(p && p->assembled && r_dev && z_dev, "bad arguments");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = stream ? (cudaStream_t)stream : p->ctx->stream;
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
     return precond_apply(p, r_dev, z_dev, s, false, nullptr, nullptr);
 }
 
@@ -333,7 +335,7 @@ int32_t ddg_local_corrections(ddg_problem *p, const double *r_dev, double *corr_
     API_BEGIN;
     REQUIRE(p && p->kind != DDG_NONE && r_dev && corr_dev && s_dev, "bad arguments");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = stream ? (cudaStream_t)stream : p->ctx->stream;
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
     return precond_apply(p, r_dev, nullptr, s, true, corr_dev, s_dev);
 }
 
@@ -341,7 +343,7 @@ int32_t ddg_apply_A(ddg_problem *p, const double *x_dev, double *y_dev, ddg_stre
     API_BEGIN;
     REQUIRE(p && p->assembled && x_dev && y_dev, "bad arguments");
     DDG_TRY(use_device(p->ctx));
-    cudaStream_t s = stream ? (cudaStream_t)stream : p->ctx->stream;
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
     return spmv(p, x_dev, y_dev, s);
 }
 

@@ -99,6 +99,8 @@ struct ChunkPlan {
 
 struct ddg_problem {
     ddg_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;  // the context's stream, or a stream of its own (served requests)
+    bool own_stream = false;
     int *d_status = nullptr;  // device status word (bits ST_*)
 
     // mesh (stage "mesh")
@@ -208,6 +210,13 @@ int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaSt
 int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
                   ddg_solve_report *rep, double *record = nullptr);
 int32_t fcg_solve_record(ddg_problem *p, int iters, double *record, int *stored);
+struct FcgRun;
+FcgRun *fcg_new();
+void fcg_delete(FcgRun *r);
+int32_t fcg_begin(FcgRun *r, ddg_problem *p, const double *x0, double rtol, int max_iter, int m);
+int32_t fcg_launch_batch(FcgRun *r);
+int32_t fcg_check(FcgRun *r, bool blocking, bool *ready, bool *done);
+int32_t fcg_end(FcgRun *r, double *x_host, ddg_solve_report *rep);
 int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o, ddg_train_report *rep);
 int32_t train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int *graphs_host, int nb,
                         double *loss, float *grad_host);

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
                 mv_acc<D>(hid, W + OFF_PSI + PSI_W1 + (D + 1) * DP, phi_o);
                 mv_acc<D>(hid, W + OFF_PSI + PSI_W1 + (2 * D + 1) * DP, phi_i);
 #pragma unroll
-                for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+                for (int o = 0; o < D; ++o) hid[o] = relu(hid[o]);
                 float out[D];
                 load_vec(out, W + OFF_PSI + PSI_B2);
                 mv_acc<D>(out, W + OFF_PSI + PSI_W2, hid);
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
             mv_acc<D>(hid, W + OFF_DEC + DEC_W1, h[p]);
             float y = W[OFF_DEC + DEC_B2];
 #pragma unroll
-            for (int o = 0; o < D; ++o) y = fmaf(W[OFF_DEC + DEC_W2 + o], fmaxf(hid[o], 0.f), y);
+            for (int o = 0; o < D; ++o) y = fmaf(W[OFF_DEC + DEC_W2 + o], relu(hid[o]), y);
             a.corr[s0 + j] = s * (double)y;
         }
     }
@@ -379,7 +379,7 @@ __device__ __forceinline__ void edge_msg_c(float (&S)[D], const float (&Pa)[D], 
         z = fmaf(W.w[OFF + o], ex, z);
         z = fmaf(W.w[OFF + DP + o], ey, z);
         z = fmaf(W.w[OFF + 2 * DP + o], en, z);
-        S[o] += fmaxf(z, 0.f);
+        S[o] += relu(z);
     }
 }
 
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss_step(const __grid_consta
             mvc_acc<D, OFF_PSI + PSI_W1 + (D + 1) * DP>(hid, W, phi_o);
             mvc_acc<D, OFF_PSI + PSI_W1 + (2 * D + 1) * DP>(hid, W, phi_i);
 #pragma unroll
-            for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+            for (int o = 0; o < D; ++o) hid[o] = relu(hid[o]);
             float out[D];
             loadc<OFF_PSI + PSI_B2>(out, W);
             mvc_acc<D, OFF_PSI + PSI_W2>(out, W, hid);
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss_step(const __grid_consta
                     mvc_acc<D, OFF_DEC + DEC_W1>(dh, W, h[p]);
                     float y = W.w[OFF_DEC + DEC_B2];
 #pragma unroll
-                    for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], fmaxf(dh[o], 0.f), y);
+                    for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], relu(dh[o]), y);
                     a.corr[s0 + j] = s * (double)y;
                 }
             } else {
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid
         mvc_acc<D, OFF_PSI + PSI_W1 + (D + 1) * DP>(hid, W, phi_o);
         mvc_acc<D, OFF_PSI + PSI_W1 + (2 * D + 1) * DP>(hid, W, phi_i);
 #pragma unroll
-        for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+        for (int o = 0; o < D; ++o) hid[o] = relu(hid[o]);
         float out[D];
         loadc<OFF_PSI + PSI_B2>(out, W);
         mvc_acc<D, OFF_PSI + PSI_W2>(out, W, hid);
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid
                 mvc_acc<D, OFF_DEC + DEC_W1>(dh, W, h);
                 float y = W.w[OFF_DEC + DEC_B2];
 #pragma unroll
-                for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], fmaxf(dh[o], 0.f), y);
+                for (int o = 0; o < D; ++o) y = fmaf(W.w[OFF_DEC + DEC_W2 + o], relu(dh[o]), y);
                 a.corr[s0 + j] = s * (double)y;
             }
         } else {
@@ -784,7 +784,7 @@ void chunk_free(ddg_problem *p) {
 
 int32_t chunk_build(ddg_problem *p, int T) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     chunk_free(p);
     ChunkPlan &cp = p->chunk;
     const int K = p->K;

@@ -35,6 +35,13 @@ constexpr int BLOCK_FLOATS = OFF_DEC + DEC_SIZE;  // 1504
 constexpr int BLOCK_BYTES = BLOCK_FLOATS * 4;     // 6016, a multiple of 16
 static_assert(BLOCK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 
+// ReLU as max(x, 0) that keeps a NaN input (max.NaN); fmaxf would return 0 for it
+__device__ __forceinline__ float relu(float x) {
+    float r;
+    asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------- bulk copy + mbarrier helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -102,7 +109,7 @@ __device__ __forceinline__ void edge_msg(float (&S)[D], const float (&Pa)[D], co
         z = fmaf(We[o], ex, z);
         z = fmaf(We[DP + o], ey, z);
         z = fmaf(We[2 * DP + o], en, z);
-        S[o] += fmaxf(z, 0.f);
+        S[o] += relu(z);
     }
 }
 

@@ -210,7 +210,7 @@ int32_t dss_autotune(ddg_problem *p) {
             return DDG_OK;
         }
     }
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     cudaEvent_t e0, e1;
     DDG_CU(cudaEventCreate(&e0));
     DDG_CU(cudaEventCreate(&e1));
@@ -431,59 +431,51 @@ static int32_t norm2(ddg_problem *p, const double *v, double *out_dev, cudaStrea
     return DDG_OK;
 }
 
-int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
-                  ddg_solve_report *rep, double *record) {
-    ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
-    const int nf = p->nf;
-    if (m < 1 || m > MAXM) {
-        set_error("m_trunc must be in [1, 16]");
-        return DDG_INVALID_ARG;
-    }
-    if (p->kr_m != m) {
-        dfree_all(c, p->a_kry);
-        p->kr_m = 0;
-    }
-    if (p->kr_m == 0) {
-        DDG_TRY(dalloc(c, p->a_kry, &p->kx, nf));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kr, nf));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kz, std::max(nf, p->n)));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)(MAXM * RB + 2 * cdiv(nf, KT) + RB + 8)));
-        DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
-        p->kr_m = m;
-    }
-    double *x = p->kx, *r = p->kr, *z = p->kz, *P = p->kP, *Q = p->kQ, *scal = p->kscal, *part = p->kpart;
-    int *flag = p->kflag;
-    const long long ld = nf;
-    DDG_CU(cudaMemsetAsync(flag, 0, sizeof(int) * F_COUNT, s));
-    DDG_CU(cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, s));
-    // x0, r0 = b - A x0
-    if (x0) {
-        DDG_CU(cudaMemcpyAsync(x, x0, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
-        DDG_TRY(spmv(p, x, z, s));
-        k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, r, nf);
-        DDG_LAUNCH_CHECK();
-    } else {
-        DDG_CU(cudaMemsetAsync(x, 0, sizeof(double) * nf, s));
-        DDG_CU(cudaMemcpyAsync(r, p->b, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
-    }
-    DDG_TRY(norm2(p, p->b, scal + S_BNORM, s));
-
-    cudaEvent_t e0, e1;
-    DDG_CU(cudaEventCreate(&e0));
-    DDG_CU(cudaEventCreate(&e1));
-    // per-iteration events of one polling window or captured period:
-    // precond start/end, local kernel start/end
-    const int L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
-    const int EW = std::max(POLL, L);
-    std::vector<cudaEvent_t> ev(4 * EW);
-    for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
+// One flexible-CG solve as a resumable state machine: begin() sets the state up,
+// launch_batch() queues the next few iterations (direct launches while the
+// direction window grows, then replays of a captured period) followed by an
+// asynchronous copy of the stop flag, check() tells (blocking or not) whether
+// that batch has finished and whether the solve is over, end() computes the
+// true residual and the report.  fcg_solve() drives it to completion; the
+// request scheduler interleaves many of them.
+struct FcgRun {
+    ddg_problem *p = nullptr;
+    cudaStream_t s = nullptr;
+    double rtol = 0.0;
+    int max_iter = 0, m = 0, nf = 0, L = 0, nb_spmv = 0;
+    long long ld = 0, off_sp = 0, off_rr = 0;
+    double *record = nullptr;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *P = nullptr, *Q = nullptr, *scal = nullptr, *part = nullptr;
+    int *flag = nullptr;
+    int *hflag = nullptr;  // pinned copy of the flags
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, batch_done = nullptr;
     double pre_ms = 0.0, loc_ms = 0.0;
     int loc_launches = 0, loc_applies = 0, launches = 0;
-    auto drain = [&](int cnt) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int per_launches = 0, per_loc_launches = 0, per_loc_applies = 0, per_global = 0;
+    bool use_graph = true;
+    int it = 0, in_flight = 0;
+
+    ~FcgRun() { release(); }
+
+    void release() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        for (auto &e : ev) cudaEventDestroy(e);
+        ev.clear();
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (batch_done) cudaEventDestroy(batch_done);
+        e0 = e1 = batch_done = nullptr;
+        if (hflag) cudaFreeHost(hflag);
+        hflag = nullptr;
+    }
+
+    void drain(int cnt) {
         for (int q = 0; q < cnt; ++q) {
             float a = 0.f, b = 0.f;
             if (cudaEventElapsedTime(&a, ev[4 * q], ev[4 * q + 1]) != cudaSuccess) a = 0.f;
@@ -492,23 +484,83 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
             pre_ms += a;
             loc_ms += b;
         }
-    };
-    const int nb_spmv = cdiv(nf, KT);
-    const long long off_sp = OFF_MD + MAXM * RB, off_rr = off_sp + 2LL * nb_spmv;
-    int hflag[F_COUNT] = {0, 0, 0, 0, 0};
+    }
+
+    int32_t begin(ddg_problem *pp, const double *x0, double rtol_, int max_iter_, int m_, double *record_) {
+        p = pp;
+        s = p->stream;
+        rtol = rtol_;
+        max_iter = max_iter_;
+        m = m_;
+        record = record_;
+        nf = p->nf;
+        ddg_ctx *c = p->ctx;
+        if (m < 1 || m > MAXM) {
+            set_error("m_trunc must be in [1, 16]");
+            return DDG_INVALID_ARG;
+        }
+        if (p->kr_m != m) {
+            dfree_all(c, p->a_kry);
+            p->kr_m = 0;
+        }
+        if (p->kr_m == 0) {
+            DDG_TRY(dalloc(c, p->a_kry, &p->kx, nf));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kr, nf));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kz, std::max(nf, p->n)));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)(MAXM * RB + 2 * cdiv(nf, KT) + RB + 8)));
+            DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
+            p->kr_m = m;
+        }
+        x = p->kx; r = p->kr; z = p->kz; P = p->kP; Q = p->kQ; scal = p->kscal; part = p->kpart;
+        flag = p->kflag;
+        ld = nf;
+        DDG_CU(cudaMallocHost(&hflag, sizeof(int) * F_COUNT));
+        for (int q = 0; q < F_COUNT; ++q) hflag[q] = 0;
+        DDG_CU(cudaMemsetAsync(flag, 0, sizeof(int) * F_COUNT, s));
+        DDG_CU(cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, s));
+        if (x0) {  // r0 = b - A x0
+            DDG_CU(cudaMemcpyAsync(x, x0, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+            DDG_TRY(spmv(p, x, z, s));
+            k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, r, nf);
+            DDG_LAUNCH_CHECK();
+        } else {
+            DDG_CU(cudaMemsetAsync(x, 0, sizeof(double) * nf, s));
+            DDG_CU(cudaMemcpyAsync(r, p->b, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+        }
+        DDG_TRY(norm2(p, p->b, scal + S_BNORM, s));
+        DDG_CU(cudaEventCreate(&e0));
+        DDG_CU(cudaEventCreate(&e1));
+        DDG_CU(cudaEventCreateWithFlags(&batch_done, cudaEventDisableTiming));
+        L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
+        ev.resize(4 * std::max(POLL, L));
+        for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
+        nb_spmv = cdiv(nf, KT);
+        off_sp = OFF_MD + MAXM * RB;
+        off_rr = off_sp + 2LL * nb_spmv;
+        use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;
+        if (record) DDG_CU(cudaMemcpyAsync(record, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+        DDG_CU(cudaEventRecord(e0, s));
+        it = 0;
+        in_flight = 0;
+        return DDG_OK;
+    }
+
     // launches one FCG iteration; q indexes the iteration's event slot
-    auto launch_iter = [&](int it, int q) -> int32_t {
+    int32_t launch_iter(int iter, int q) {
         Window win{};
-        win.W = std::min(it, m);
-        for (int j = 0; j < win.W; ++j) win.slot[j] = (it - win.W + j) % m;
-        win.snew = it % m;
+        win.W = std::min(iter, m);
+        for (int j = 0; j < win.W; ++j) win.slot[j] = (iter - win.W + j) % m;
+        win.snew = iter % m;
         cudaEvent_t *evq = ev.data() + 4 * q;
         DDG_CU(record_event(evq[0], s));
         DDG_TRY(precond_core(p, r, z, s, flag, true, p->kind != DDG_NONE ? evq + 2 : nullptr, &launches));
         DDG_CU(record_event(evq[1], s));
         if (p->kind != DDG_NONE) {
             ++loc_applies;
-            loc_launches += (p->kind == DDG_DDM_GNN && p->dss_sched == 1) ? p->model->kbar : 1;
+            loc_launches += (p->kind == DDG_DDM_GNN && p->dss_sched >= 1) ? p->model->kbar : 1;
         }
         double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
         if (win.W > 0) {
@@ -521,26 +573,15 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
         k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
         launches += 3;
         DDG_LAUNCHES(3);
-        if (record) DDG_CU(cudaMemcpyAsync(record + (size_t)(it + 1) * nf, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+        if (record)
+            DDG_CU(cudaMemcpyAsync(record + (size_t)(iter + 1) * nf, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
         return DDG_OK;
-    };
-    auto poll = [&](int window) -> int32_t {
-        DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
-        DDG_CU(cudaStreamSynchronize(s));
-        drain(window);
-        return DDG_OK;
-    };
+    }
+
     // The first m iterations grow the direction window; from iteration m on the
     // ring slots repeat with period m, so one period is captured as a CUDA graph
-    // and replayed, polling the stop flag once per replay.
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    int per_launches = 0, per_loc_launches = 0, per_loc_applies = 0, per_global = 0;
-    const bool use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;
-    if (record) DDG_CU(cudaMemcpyAsync(record, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
-    DDG_CU(cudaEventRecord(e0, s));
-    int it = 0, in_window = 0;
-    while (it < max_iter) {
+    // and replayed.  Queues one batch and the copy of the stop flag behind it.
+    int32_t launch_batch() {
         if (use_graph && it >= m && it % m == 0 && max_iter - it >= L) {
             if (!gexec) {
                 // the capture counts the period's launches once; every later replay adds them again
@@ -565,60 +606,101 @@ int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, i
             }
             DDG_CU(cudaGraphLaunch(gexec, s));
             it += L;
-            DDG_TRY(poll(L));
-            if (hflag[F_STOP]) break;
-            continue;
+            in_flight = L;
+        } else {
+            int n = 0;
+            do {
+                DDG_TRY(launch_iter(it, n));
+                ++it;
+                ++n;
+            } while (n < POLL && it < max_iter && !(use_graph && it == m));
+            in_flight = n;
         }
-        DDG_TRY(launch_iter(it, in_window));
-        ++it;
-        ++in_window;
-        if (in_window == POLL || it == max_iter || (use_graph && it == m)) {
-            DDG_TRY(poll(in_window));
-            in_window = 0;
-            if (hflag[F_STOP]) break;
-        }
+        DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+        DDG_CU(cudaEventRecord(batch_done, s));
+        return DDG_OK;
     }
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-    DDG_CU(cudaEventRecord(e1, s));
-    DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
-    double hs[S_COUNT];
-    DDG_CU(cudaMemcpyAsync(hs, scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
-    // true residual |b - A x| / |b|
-    DDG_TRY(spmv(p, x, z, s));
-    k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, z, nf);
-    DDG_LAUNCH_CHECK();
-    double *tr = scal + S_COUNT;
-    DDG_TRY(norm2(p, z, tr, s));
-    double htr = 0.0;
-    DDG_CU(cudaMemcpyAsync(&htr, tr, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (x_host) {
-        k_full_solution<<<cdiv(p->n, KT), KT, 0, s>>>(x, p->g, p->free_id, p->n, z);
+
+    // *ready: the queued batch has finished; *done: the solve is over
+    int32_t check(bool blocking, bool *ready, bool *done) {
+        if (blocking) {
+            DDG_CU(cudaEventSynchronize(batch_done));
+        } else {
+            cudaError_t q = cudaEventQuery(batch_done);
+            if (q == cudaErrorNotReady) {
+                *ready = false;
+                *done = false;
+                return DDG_OK;
+            }
+            DDG_CU(q);
+        }
+        *ready = true;
+        drain(in_flight);
+        in_flight = 0;
+        *done = hflag[F_STOP] != 0 || it >= max_iter;
+        return DDG_OK;
+    }
+
+    int32_t end(double *x_host, ddg_solve_report *rep) {
+        DDG_CU(cudaEventRecord(e1, s));
+        DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+        double hs[S_COUNT];
+        DDG_CU(cudaMemcpyAsync(hs, scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+        // true residual |b - A x| / |b|
+        DDG_TRY(spmv(p, x, z, s));
+        k_residual<<<cdiv(nf, KT), KT, 0, s>>>(p->b, z, z, nf);
         DDG_LAUNCH_CHECK();
-        DDG_CU(cudaMemcpyAsync(x_host, z, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s));
+        double *tr = scal + S_COUNT;
+        DDG_TRY(norm2(p, z, tr, s));
+        double htr = 0.0;
+        DDG_CU(cudaMemcpyAsync(&htr, tr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (x_host) {
+            k_full_solution<<<cdiv(p->n, KT), KT, 0, s>>>(x, p->g, p->free_id, p->n, z);
+            DDG_LAUNCH_CHECK();
+            DDG_CU(cudaMemcpyAsync(x_host, z, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s));
+        }
+        DDG_CU(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ddg_solve_report rp{};
+        rp.iterations = hflag[F_ITERS];
+        rp.rel_residual = hs[S_REL];
+        rp.true_rel_residual = htr / hs[S_BNORM];
+        rp.solve_ms = ms;
+        rp.precond_ms = pre_ms;
+        rp.local_ms = loc_ms;
+        rp.local_launches = loc_launches;
+        rp.launches = launches;
+        rp.local_applies = loc_applies;
+        rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
+        rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
+        if (rep) *rep = rp;
+        release();
+        if (rp.status == DDG_BREAKDOWN) set_error("FCG breakdown: p.q <= 0 or a non-finite scalar");
+        if (rp.status == DDG_NOT_CONVERGED) set_error("FCG reached max_iter");
+        return rp.status;
     }
-    DDG_CU(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (auto &e : ev) cudaEventDestroy(e);
-    ddg_solve_report rp{};
-    rp.iterations = hflag[F_ITERS];
-    rp.rel_residual = hs[S_REL];
-    rp.true_rel_residual = htr / hs[S_BNORM];
-    rp.solve_ms = ms;
-    rp.precond_ms = pre_ms;
-    rp.local_ms = loc_ms;
-    rp.local_launches = loc_launches;
-    rp.launches = launches;
-    rp.local_applies = loc_applies;
-    rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
-    rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
-    if (rep) *rep = rp;
-    if (rp.status == DDG_BREAKDOWN) set_error("FCG breakdown: p.q <= 0 or a non-finite scalar");
-    if (rp.status == DDG_NOT_CONVERGED) set_error("FCG reached max_iter");
-    return rp.status;
+};
+
+FcgRun *fcg_new() { return new FcgRun(); }
+void fcg_delete(FcgRun *r) { delete r; }
+int32_t fcg_begin(FcgRun *r, ddg_problem *p, const double *x0, double rtol, int max_iter, int m) {
+    return r->begin(p, x0, rtol, max_iter, m, nullptr);
+}
+int32_t fcg_launch_batch(FcgRun *r) { return r->launch_batch(); }
+int32_t fcg_check(FcgRun *r, bool blocking, bool *ready, bool *done) { return r->check(blocking, ready, done); }
+int32_t fcg_end(FcgRun *r, double *x_host, ddg_solve_report *rep) { return r->end(x_host, rep); }
+
+int32_t fcg_solve(ddg_problem *p, const double *x0, double rtol, int max_iter, int m, double *x_host,
+                  ddg_solve_report *rep, double *record) {
+    FcgRun run;
+    DDG_TRY(run.begin(p, x0, rtol, max_iter, m, record));
+    bool ready = false, done = false;
+    while (!done) {
+        DDG_TRY(run.launch_batch());
+        DDG_TRY(run.check(true, &ready, &done));
+    }
+    return run.end(x_host, rep);
 }
 
 // Runs PCG (FCG with m = 1) with the current preconditioner for at most iters - 1

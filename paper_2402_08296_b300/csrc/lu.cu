@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int
 
 int32_t lu_build(ddg_problem *p) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     const int K = p->K;
     std::vector<int> hp(K + 1);
     DDG_CU(cudaMemcpyAsync(hp.data(), p->sub_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));

@@ -129,7 +129,7 @@ __global__ void k_free_ids(const uint8_t *dir, const double *xy, int n, int *fre
 
 int32_t mesh_build(ddg_problem *p, const uint8_t *dirichlet_host) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     const int n = p->n, t = p->t;
     int *cnt = nullptr, *fill = nullptr, *deg = nullptr;
     uint8_t *bnd = nullptr;
@@ -320,7 +320,7 @@ __global__ void k_assemble(const double *xy, const int *tri, const int *tptr, co
 
 int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal_host, const double *g_nodal_host) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
     chunk_free(p);

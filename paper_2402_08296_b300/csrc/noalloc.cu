@@ -96,7 +96,7 @@ extern "C" int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, 
     DDG_CU(cudaSetDevice(p->ctx->device));
     double *partials = nullptr;
     DDG_TRY(partials_for_device(p->ctx->device, &partials));
-    cudaStream_t s = stream ? (cudaStream_t)stream : p->ctx->stream;
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
     k_spmv_dot_noalloc<<<nb, NOALLOC_T, 0, s>>>(p->rowptr, p->col, p->val, x_dev, y_dev, p->nf, partials);
     DDG_LAUNCH_CHECK();
     k_dot_final_noalloc<<<1, NOALLOC_T, 0, s>>>(partials, nb, xy_dev);

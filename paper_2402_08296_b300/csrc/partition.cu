@@ -92,7 +92,7 @@ __global__ void k_part_from_segments(const int *L, int nf, const int *seg_start,
 
 static int32_t rcb(ddg_problem *p, int K) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     const int nf = p->nf;
     int *Lx, *Ly, *Ln, *flag, *scan;
     uint8_t *side;
@@ -542,7 +542,7 @@ __global__ void k_gj_update(double *A, int K, int k, const double *prow, const d
 
 int32_t coarse_build(ddg_problem *p) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     const int K = p->K;
     DDG_TRY(dalloc(c, p->a_part, &p->A0, (size_t)K * K));
     DDG_TRY(dalloc(c, p->a_part, &p->A0inv, (size_t)K * K));
@@ -592,7 +592,7 @@ __global__ void k_iota_i(int *a, int n) {
 
 int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) {
     ddg_ctx *c = p->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = p->stream;
     dfree_all(c, p->a_kry);
     dfree_all(c, p->a_pre);
     chunk_free(p);

@@ -46,10 +46,10 @@ void dfree_all(ddg_ctx *ctx, Allocs &a) {
 
 int32_t check_status(ddg_problem *p, const char *where) {
     int st = 0;
-    DDG_CU(cudaMemcpyAsync(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->ctx->stream));
-    DDG_CU(cudaStreamSynchronize(p->ctx->stream));
+    DDG_CU(cudaMemcpyAsync(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    DDG_CU(cudaStreamSynchronize(p->stream));
     if (st == 0) return DDG_OK;
-    DDG_CU(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->ctx->stream));
+    DDG_CU(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
     std::string w(where);
     if (st & ST_BAD_MESH) {
         set_error(w + ": degenerate/inverted triangle or node degree above the cap");

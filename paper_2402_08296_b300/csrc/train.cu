@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TR_T) k_tr_fwd(TrainArgs a) {
             mv_acc<1>(hid, Wsh + OFF_PSI + PSI_W1 + D * DP, cc);
             mv_acc<D>(hid, Wsh + OFF_PSI + PSI_W1 + (D + 1) * DP, fo);
             mv_acc<D>(hid, Wsh + OFF_PSI + PSI_W1 + (2 * D + 1) * DP, fi);
-            for (int o = 0; o < D; ++o) hid[o] = fmaxf(hid[o], 0.f);
+            for (int o = 0; o < D; ++o) hid[o] = relu(hid[o]);
             float out[D];
             load_vec(out, Wsh + OFF_PSI + PSI_B2);
             mv_acc<D>(out, Wsh + OFF_PSI + PSI_W2, hid);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(TR_T) k_tr_fwd(TrainArgs a) {
                 load_vec(dh, Wsh + OFF_DEC + DEC_B1);
                 mv_acc<D>(dh, Wsh + OFF_DEC + DEC_W1, h);
                 float y = Wsh[OFF_DEC + DEC_B2];
-                for (int o = 0; o < D; ++o) y = fmaf(Wsh[OFF_DEC + DEC_W2 + o], fmaxf(dh[o], 0.f), y);
+                for (int o = 0; o < D; ++o) y = fmaf(Wsh[OFF_DEC + DEC_W2 + o], relu(dh[o]), y);
                 a.rhat[(long long)blk * a.NK + kb0 + j] = y;
             }
         }
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TR_T) k_tr_bwd(TrainArgs a) {
             if (inner) gy = a.ghat[(long long)blk * a.NK + kb0 + j];
             float du[D];
             for (int o = 0; o < D; ++o) {
-                gacc(gsh, OFF_DEC + DEC_W2 + o, gy * fmaxf(u[o], 0.f));
+                gacc(gsh, OFF_DEC + DEC_W2 + o, gy * relu(u[o]));
                 du[o] = u[o] > 0.f ? gy * Wsh[OFF_DEC + DEC_W2 + o] : 0.f;
                 gacc(gsh, OFF_DEC + DEC_B1 + o, du[o]);
             }
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(TR_T) k_tr_bwd(TrainArgs a) {
             for (int o = 0; o < D; ++o) dout_v[o] = act ? a.alpha * *scv(a, SC_DH, o, nb0 + j) : 0.f;
             for (int o = 0; o < D; ++o) gacc(gsh, OFF_PSI + PSI_B2 + o, dout_v[o]);
             for (int i = 0; i < D; ++i) {
-                const float ai = fmaxf(u[i], 0.f);
+                const float ai = relu(u[i]);
                 float v = 0.f;
                 for (int o = 0; o < D; ++o) {
                     gacc(gsh, OFF_PSI + PSI_W2 + i * DP + o, dout_v[o] * ai);
@@ -603,7 +603,7 @@ struct Trainer {
     float *c = nullptr, *hsave = nullptr, *rhat = nullptr, *ghat = nullptr, *res_k = nullptr, *scr = nullptr;
 
     int32_t init() {
-        cudaStream_t s = p->ctx->stream;
+        cudaStream_t s = p->stream;
         const int K = p->K;
         per_block = 11 * D * D + 15 * D + 1;
         // local matrices
@@ -675,7 +675,7 @@ struct Trainer {
 
     // loss (mean over the batch) and gradient in gflat for samples (graph, residual pointer)
     int32_t loss_grad(const std::vector<int> &graphs, const std::vector<const double *> &res, double *loss_out) {
-        cudaStream_t s = p->ctx->stream;
+        cudaStream_t s = p->stream;
         const int B = (int)graphs.size();
         std::vector<int> nb(B + 1, 0), kb(B + 1, 0);
         for (int b = 0; b < B; ++b) {
@@ -740,7 +740,7 @@ struct Trainer {
     }
 
     int32_t adam_step(int t, float lr, float clip) {
-        cudaStream_t s = p->ctx->stream;
+        cudaStream_t s = p->stream;
         const long long nw = (long long)m->kbar * per_block;
         float bc1 = 1.f - std::pow(0.9f, (float)t), bc2 = 1.f - std::pow(0.999f, (float)t);
         k_tr_adam<<<cdiv(nw, 256), 256, 0, s>>>(m->w, gflat, m1, m2, nw, stats, lr, clip, bc1, bc2);
@@ -760,7 +760,7 @@ static uint64_t sm_next(uint64_t &state) {
 }
 
 int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o, ddg_train_report *rep) {
-    cudaStream_t s = p->ctx->stream;
+    cudaStream_t s = p->stream;
     cudaEvent_t e0, e1;
     DDG_CU(cudaEventCreate(&e0));
     DDG_CU(cudaEventCreate(&e1));
