@@ -25,7 +25,8 @@
  *    default stream, so pass cudaStreamLegacy to run on that one.
  *  - Indices are int32, zero-based.  "free" nodes are the mesh nodes that are
  *    not Dirichlet nodes, numbered in ascending mesh order.
- *  - A context and everything created from it is not thread-safe.
+ *  - A context and everything created from it is not thread-safe, except
+ *    ddg_submit, ddg_poll and ddg_serve_stats, which any thread may call.
  */
 #ifndef DDG_H
 #define DDG_H
@@ -49,6 +50,7 @@ enum ddg_status {
     DDG_CUDA_ERROR = -3,    /* a CUDA runtime call failed */
     DDG_NOT_CONVERGED = -4, /* max_iter reached */
     DDG_BREAKDOWN = -5,     /* p.q <= 0 or a non-finite scalar in the Krylov loop */
+    DDG_PENDING = -8,       /* ddg_poll: the request has not finished yet */
     DDG_BAD_MESH = -9,      /* degenerate or inverted triangle, or a node of too high degree */
     DDG_TOO_LARGE = -10     /* a subdomain or node list beyond a kernel's on-chip capacity */
 };
@@ -248,6 +250,45 @@ int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, double *y_d
  * report's status. */
 int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,
                       double *x_host, ddg_solve_report *report);
+
+/* ---- serving (continuous batching of independent solves) ------------- */
+
+typedef struct ddg_solve_opts {
+    int32_t kind;            /* DDG_DDM_GNN, DDG_DDM_LU or DDG_NONE */
+    uint32_t flags;          /* DDG_COARSE, DDG_POU_PROLONG */
+    const ddg_model *model;  /* for DDG_DDM_GNN; must outlive the request */
+    int32_t K;               /* subdomains; 0 = round(n_free / 1000) */
+    int32_t overlap;         /* overlap layers */
+    double rtol;
+    int32_t max_iter;
+    int32_t m_trunc;
+} ddg_solve_opts;
+
+typedef struct ddg_serve_summary {
+    uint64_t completed, failed, pending, active;
+    uint64_t reserved_bytes;  /* device memory estimated for the admitted requests */
+    uint64_t device_bytes;    /* device memory held by the context */
+    double p50_ms, p99_ms;    /* latency from submit to result, over completed requests */
+    double solves_per_s;      /* completed requests / (last completion - first submit) */
+} ddg_serve_summary;
+
+/* Queue the solve of -Lap(u) = f, u = g (data family of Eqs. 24-25, r[0..8])
+ * on the given mesh (copied) and return a ticket.  A scheduler thread owned by
+ * the context admits queued requests in arrival order while fewer than
+ * max_active run and their estimated device memory fits the context's HBM
+ * budget, sets each up on a stream of its own and advances all running
+ * solves a batch of iterations at a time, so their GPU work overlaps.
+ * Thread-safe with ddg_poll and ddg_serve_stats. */
+int32_t ddg_submit(ddg_ctx *ctx, int32_t n_nodes, const double *xy, int32_t n_tri, const int32_t *tri,
+                   const double r[9], const ddg_solve_opts *opts, uint64_t *ticket);
+/* DDG_PENDING while the request is queued or running; afterwards its final
+ * status (DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN or a set-up error), the
+ * report (solve_ms = wall time from admission to the result) and, if x_host
+ * is not NULL, the nodal solution (n_nodes).  A ticket is collected once. */
+int32_t ddg_poll(ddg_ctx *ctx, uint64_t ticket, ddg_solve_report *report, double *x_host);
+/* Most requests in flight at once (default 64). */
+int32_t ddg_serve_config(ddg_ctx *ctx, int32_t max_active);
+int32_t ddg_serve_stats(ddg_ctx *ctx, ddg_serve_summary *out);
 
 #ifdef __cplusplus
 }

@@ -31,10 +31,11 @@ DDG_OOM = -2
 DDG_CUDA_ERROR = -3
 DDG_NOT_CONVERGED = -4
 DDG_BREAKDOWN = -5
+DDG_PENDING = -8
 DDG_BAD_MESH = -9
 DDG_TOO_LARGE = -10
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR", -4: "NOT_CONVERGED",
-                -5: "BREAKDOWN", -9: "BAD_MESH", -10: "TOO_LARGE"}
+                -5: "BREAKDOWN", -8: "PENDING", -9: "BAD_MESH", -10: "TOO_LARGE"}
 
 DDG_NONE, DDG_DDM_LU, DDG_DDM_GNN = 0, 1, 2
 DDG_COARSE, DDG_POU_PROLONG = 1, 2
@@ -71,6 +72,20 @@ class ddg_train_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ddg_solve_opts(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("flags", ctypes.c_uint32), ("model", _p), ("K", _i32), ("overlap", _i32),
+                ("rtol", _f64), ("max_iter", _i32), ("m_trunc", _i32)]
+
+
+class ddg_serve_summary(ctypes.Structure):
+    _fields_ = [("completed", _u64), ("failed", _u64), ("pending", _u64), ("active", _u64),
+                ("reserved_bytes", _u64), ("device_bytes", _u64), ("p50_ms", _f64), ("p99_ms", _f64),
+                ("solves_per_s", _f64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _SIGS = {
     "ddg_create": [_i32, _sz, ctypes.POINTER(_p)],
     "ddg_destroy": [_p],
@@ -97,6 +112,10 @@ _SIGS = {
     "ddg_apply_A_dot_noalloc": [_p, _p, _p, _p, _p],
     "ddg_train_local_model": [_p, _p, ctypes.POINTER(ddg_train_opts), ctypes.POINTER(ddg_train_report)],
     "ddg_train_loss_grad": [_p, _p, _p, _p, _i32, ctypes.POINTER(_f64), _p],
+    "ddg_submit": [_p, _i32, _p, _i32, _p, _p, ctypes.POINTER(ddg_solve_opts), ctypes.POINTER(_u64)],
+    "ddg_poll": [_p, _u64, ctypes.POINTER(ddg_solve_report), _p],
+    "ddg_serve_config": [_p, _i32],
+    "ddg_serve_stats": [_p, ctypes.POINTER(ddg_serve_summary)],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
 }
 for _name, _args in _SIGS.items():
@@ -351,3 +370,38 @@ def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: 
     if st not in (DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN):
         raise DdgError(st, "ddg_fcg_solve")
     return rep.as_dict(), x
+
+
+def ddg_submit(ctx, xy, tri, r, kind: int, model=None, flags: int = DDG_COARSE, K: int = 0, overlap: int = 2,
+               rtol: float = 1e-6, max_iter: int = 2000, m_trunc: int = 10) -> int:
+    """Queue a solve; returns its ticket."""
+    xy_a, xy_p = _host(xy, np.float64)
+    tri_a, tri_p = _host(tri, np.int32)
+    r_a, r_p = _host(r, np.float64)
+    o = ddg_solve_opts(kind, flags, model, K, overlap, rtol, max_iter, m_trunc)
+    t = _u64()
+    _check(lib.ddg_submit(ctx, xy_a.shape[0], xy_p, tri_a.shape[0], tri_p, r_p, ctypes.byref(o), ctypes.byref(t)),
+           "ddg_submit")
+    return int(t.value)
+
+
+def ddg_poll(ctx, ticket: int, n_nodes: int | None = None):
+    """(status, report dict, x or None); status DDG_PENDING while the request runs."""
+    rep = ddg_solve_report()
+    x = np.zeros(n_nodes, np.float64) if n_nodes else None
+    st = lib.ddg_poll(ctx, ticket, ctypes.byref(rep), x.ctypes.data_as(_p) if x is not None else None)
+    if st == DDG_PENDING:
+        return st, None, None
+    if st == DDG_INVALID_ARG:
+        raise DdgError(st, "ddg_poll")
+    return st, rep.as_dict(), x
+
+
+def ddg_serve_config(ctx, max_active: int) -> None:
+    _check(lib.ddg_serve_config(ctx, max_active), "ddg_serve_config")
+
+
+def ddg_serve_stats(ctx) -> dict:
+    out = ddg_serve_summary()
+    _check(lib.ddg_serve_stats(ctx, ctypes.byref(out)), "ddg_serve_stats")
+    return out.as_dict()

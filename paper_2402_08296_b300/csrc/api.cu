@@ -6,9 +6,6 @@
 #include <algorithm>
 #include <cstring>
 
-namespace ddg {
-const char *last_error_cstr();
-}
 
 using namespace ddg;
 
@@ -25,6 +22,42 @@ static int32_t use_device(ddg_ctx *c) {
     DDG_CU(cudaSetDevice(c->device));
     return DDG_OK;
 }
+
+namespace ddg {
+
+int32_t problem_create(ddg_ctx *c, int n_nodes, const double *xy, int n_tri, const int *tri, const uint8_t *dirichlet,
+                       cudaStream_t stream, bool own_stream, ddg_problem **out) {
+    ddg_problem *p = new ddg_problem();
+    p->ctx = c;
+    p->stream = stream;
+    p->own_stream = own_stream;
+    p->n = n_nodes;
+    p->t = n_tri;
+    for (ddg::Allocs *a : {&p->a_mesh, &p->a_matrix, &p->a_part, &p->a_pre, &p->a_kry, &p->chunk.allocs}) {
+        a->stream = stream;
+        a->use_stream = true;
+    }
+    int32_t st = DDG_OK;
+    do {
+        if ((st = dalloc(c, p->a_mesh, &p->d_status, 1)) != DDG_OK) break;
+        if ((st = dalloc(c, p->a_mesh, &p->xy, 2LL * n_nodes)) != DDG_OK) break;
+        if ((st = dalloc(c, p->a_mesh, &p->tri, 3LL * n_tri)) != DDG_OK) break;
+        cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream);
+        cudaMemcpyAsync(p->xy, xy, sizeof(double) * 2 * n_nodes, cudaMemcpyHostToDevice, p->stream);
+        cudaMemcpyAsync(p->tri, tri, sizeof(int) * 3 * n_tri, cudaMemcpyHostToDevice, p->stream);
+        st = mesh_build(p, dirichlet);
+    } while (0);
+    if (st != DDG_OK) {
+        std::string msg = last_error_cstr();
+        ddg_problem_destroy(p);
+        set_error(msg);
+        return st;
+    }
+    *out = p;
+    return DDG_OK;
+}
+
+}  // namespace ddg
 
 extern "C" {
 
@@ -53,6 +86,7 @@ int32_t ddg_create(int32_t device, size_t hbm_budget_bytes, ddg_ctx **out) {
 int32_t ddg_destroy(ddg_ctx *c) {
     API_BEGIN;
     if (!c) return DDG_OK;
+    server_stop(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaStreamDestroy(c->stream);
@@ -63,7 +97,7 @@ int32_t ddg_destroy(ddg_ctx *c) {
 int32_t ddg_memory_in_use(ddg_ctx *c, size_t *bytes) {
     API_BEGIN;
     REQUIRE(c && bytes, "NULL argument");
-    *bytes = c->in_use;
+    *bytes = c->in_use.load();
     return DDG_OK;
 }
 
@@ -88,29 +122,7 @@ int32_t ddg_mesh_upload(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n
     REQUIRE(c && xy && tri && out, "NULL argument");
     REQUIRE(n_nodes >= 3 && n_tri >= 1, "mesh needs at least one triangle");
     DDG_TRY(use_device(c));
-    ddg_problem *p = new ddg_problem();
-    p->ctx = c;
-    p->stream = c->stream;
-    p->n = n_nodes;
-    p->t = n_tri;
-    int32_t st = DDG_OK;
-    do {
-        if ((st = dalloc(c, p->a_mesh, &p->d_status, 1)) != DDG_OK) break;
-        if ((st = dalloc(c, p->a_mesh, &p->xy, 2LL * n_nodes)) != DDG_OK) break;
-        if ((st = dalloc(c, p->a_mesh, &p->tri, 3LL * n_tri)) != DDG_OK) break;
-        cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream);
-        cudaMemcpyAsync(p->xy, xy, sizeof(double) * 2 * n_nodes, cudaMemcpyHostToDevice, p->stream);
-        cudaMemcpyAsync(p->tri, tri, sizeof(int) * 3 * n_tri, cudaMemcpyHostToDevice, p->stream);
-        st = mesh_build(p, dirichlet);
-    } while (0);
-    if (st != DDG_OK) {
-        std::string msg = last_error_cstr();
-        ddg_problem_destroy(p);
-        set_error(msg);
-        return st;
-    }
-    *out = p;
-    return DDG_OK;
+    return problem_create(c, n_nodes, xy, n_tri, tri, dirichlet, c->stream, false, out);
 }
 
 int32_t ddg_problem_destroy(ddg_problem *p) {
@@ -124,6 +136,8 @@ int32_t ddg_problem_destroy(ddg_problem *p) {
     dfree_all(c, p->a_part);
     dfree_all(c, p->a_matrix);
     dfree_all(c, p->a_mesh);
+    if (p->hflag_pinned) cudaFreeHost(p->hflag_pinned);
+    cudaStreamSynchronize(p->stream);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
     return DDG_OK;

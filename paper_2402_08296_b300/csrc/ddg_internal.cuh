@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -53,10 +55,16 @@ constexpr int DSS_D = 10;          // latent size compiled into the GNN kernel
 constexpr int DSS_THREADS = 512;
 constexpr int DSS_MAX_NODES = 2048; // local graph nodes (unknowns + halo) per CTA
 
+struct Server;  // request scheduler (serve.cu)
+
 // ---------------------------------------------------------------- allocation
+// device allocations of one stage; stream-ordered (no device-wide synchronisation on
+// free) when `stream` is set, as for the buffers of a problem
 struct Allocs {
     std::vector<void *> ptrs;
     std::vector<size_t> sizes;
+    cudaStream_t stream = nullptr;
+    bool use_stream = false;
 };
 
 }  // namespace ddg
@@ -65,7 +73,10 @@ struct ddg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t budget = 0;
-    size_t in_use = 0;
+    std::atomic<size_t> in_use{0};
+    ddg::Server *server = nullptr;  // started by the first ddg_submit
+    std::mutex server_mu;
+    std::mutex tune_mu;             // guards `tuned` (set-up may run on the scheduler thread)
     // GNN schedule chosen by the autotuner, cached per decomposition shape (K, graph nodes, largest graph)
     struct Tuned {
         long long K, nodes, max_loc;
@@ -165,6 +176,7 @@ struct ddg_problem {
     ddg::Allocs a_pre;
 
     // Krylov workspace (stage "krylov")
+    int *hflag_pinned = nullptr;  // host copy of the Krylov flags (pinned)
     int kr_m = 0;
     double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kP = nullptr, *kQ = nullptr, *kscal = nullptr;
     double *kpart = nullptr;   // block partials of reductions
@@ -183,6 +195,10 @@ int32_t dalloc(ddg_ctx *ctx, Allocs &a, T **p, size_t n) {
 void dfree_all(ddg_ctx *ctx, Allocs &a);
 
 int32_t check_status(ddg_problem *p, const char *where);
+const char *last_error_cstr();
+int32_t problem_create(ddg_ctx *c, int n_nodes, const double *xy, int n_tri, const int *tri, const uint8_t *dirichlet,
+                       cudaStream_t stream, bool own_stream, ddg_problem **out);
+void server_stop(ddg_ctx *c);
 
 // primitives (prims.cu)
 int32_t scan_exclusive(ddg_ctx *ctx, const int *in, int *out, int n, int *total_host, cudaStream_t s);

@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(CH_T) k_chunk_build(const int *c_graph, const 
 }
 
 void chunk_free(ddg_problem *p) {
-    dfree_all(p->ctx, p->chunk.allocs);
+    dfree_all(p->ctx, p->chunk.allocs);  // keeps the stage's stream settings
     ChunkPlan empty;
     p->chunk.T = p->chunk.nchunks = p->chunk.max_need = 0;
     p->chunk.c_graph = p->chunk.c_n0 = p->chunk.c_own = p->chunk.c_need_off = p->chunk.c_need_n = nullptr;

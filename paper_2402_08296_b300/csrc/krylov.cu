@@ -203,10 +203,19 @@ int32_t dss_autotune(ddg_problem *p) {
         if (p->dss_sched == 2) DDG_TRY(chunk_build(p, envT ? atoi(envT) : 192));
         return DDG_OK;
     }
-    for (const auto &t : p->ctx->tuned) {
-        if (t.K == p->K && t.nodes == p->sum_loc && t.max_loc == p->max_loc) {
-            p->dss_sched = t.sched;
-            if (t.sched == 2) DDG_TRY(chunk_build(p, t.T));
+    {
+        int cached = -1, cachedT = 0;
+        {
+            std::lock_guard<std::mutex> lock(p->ctx->tune_mu);
+            for (const auto &t : p->ctx->tuned)
+                if (t.K == p->K && t.nodes == p->sum_loc && t.max_loc == p->max_loc) {
+                    cached = t.sched;
+                    cachedT = t.T;
+                }
+        }
+        if (cached >= 0) {
+            p->dss_sched = cached;
+            if (cached == 2) DDG_TRY(chunk_build(p, cachedT));
             return DDG_OK;
         }
     }
@@ -241,7 +250,10 @@ int32_t dss_autotune(ddg_problem *p) {
     } else {
         chunk_free(p);
     }
-    p->ctx->tuned.push_back({(long long)p->K, p->sum_loc, (long long)p->max_loc, pick, pickT});
+    {
+        std::lock_guard<std::mutex> lock(p->ctx->tune_mu);
+        p->ctx->tuned.push_back({(long long)p->K, p->sum_loc, (long long)p->max_loc, pick, pickT});
+    }
     return check_status(p, "GNN schedule selection");
 }
 
@@ -471,8 +483,7 @@ struct FcgRun {
         if (e1) cudaEventDestroy(e1);
         if (batch_done) cudaEventDestroy(batch_done);
         e0 = e1 = batch_done = nullptr;
-        if (hflag) cudaFreeHost(hflag);
-        hflag = nullptr;
+        hflag = nullptr;  // owned by the problem
     }
 
     void drain(int cnt) {
@@ -517,7 +528,8 @@ struct FcgRun {
         x = p->kx; r = p->kr; z = p->kz; P = p->kP; Q = p->kQ; scal = p->kscal; part = p->kpart;
         flag = p->kflag;
         ld = nf;
-        DDG_CU(cudaMallocHost(&hflag, sizeof(int) * F_COUNT));
+        if (!p->hflag_pinned) DDG_CU(cudaMallocHost(&p->hflag_pinned, sizeof(int) * F_COUNT));
+        hflag = p->hflag_pinned;
         for (int q = 0; q < F_COUNT; ++q) hflag[q] = 0;
         DDG_CU(cudaMemsetAsync(flag, 0, sizeof(int) * F_COUNT, s));
         DDG_CU(cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, s));

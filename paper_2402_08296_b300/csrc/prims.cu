@@ -18,12 +18,12 @@ void clear_error() { g_last_error.clear(); }
 const char *last_error_cstr() { return g_last_error.c_str(); }
 
 int32_t dmalloc(ddg_ctx *ctx, Allocs &a, void **p, size_t bytes) {
-    if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
-        set_error("HBM budget exceeded: " + std::to_string(ctx->in_use + bytes) + " > " +
+    if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget) {
+        set_error("HBM budget exceeded: " + std::to_string(ctx->in_use.load() + bytes) + " > " +
                   std::to_string(ctx->budget) + " bytes");
         return DDG_OOM;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = a.use_stream ? cudaMallocAsync(p, bytes, a.stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
@@ -37,7 +37,7 @@ int32_t dmalloc(ddg_ctx *ctx, Allocs &a, void **p, size_t bytes) {
 
 void dfree_all(ddg_ctx *ctx, Allocs &a) {
     for (size_t i = 0; i < a.ptrs.size(); ++i) {
-        cudaFree(a.ptrs[i]);
+        if (a.use_stream) cudaFreeAsync(a.ptrs[i], a.stream); else cudaFree(a.ptrs[i]);
         ctx->in_use -= a.sizes[i];
     }
     a.ptrs.clear();

@@ -1,0 +1,94 @@
+"""Serving: requests that arrive while others run are admitted and overlap on the GPU,
+and every result equals the stand-alone solve of the same problem (bitwise)."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _wait(ddg, ctx, tickets, sizes, timeout=300.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t, n in zip(tickets, sizes):
+            if t in out:
+                continue
+            st, rep, x = ddg.ddg_poll(ctx, t, n)
+            if st != ddg.DDG_PENDING:
+                out[t] = (st, rep, x)
+        assert time.time() - t0 < timeout, "requests did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def test_results_alone_equal_results_in_the_mix():
+    import paper_2402_08296_b300 as ddg
+    ctx = ddg.ddg_create(0)
+    W = synth.dss_weights(30, 10, 21, bias_scale=0.05)
+    m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
+    try:
+        reqs = []
+        for i, n in enumerate([6000, 20000, 9000, 40000, 12000, 5000]):
+            mesh = synth.star_mesh(n, seed=300 + i)
+            kind = ddg.DDG_DDM_GNN if i % 2 == 0 else ddg.DDG_DDM_LU
+            reqs.append((mesh, synth.poly_coeffs(300 + i), kind))
+        # alone: one after the other, each with the blocking solver
+        alone = []
+        for mesh, r, kind in reqs:
+            p = ddg.ddg_mesh_upload(ctx, mesh.xy, mesh.tri)
+            ddg.ddg_assemble_poly(p, r)
+            K = max(1, int(ddg.ddg_problem_info(p)["n_free"] / 1000 + 0.5))
+            ddg.ddg_partition(p, K, 2)
+            ddg.ddg_setup_precond(p, kind, m if kind == ddg.DDG_DDM_GNN else None, ddg.DDG_COARSE)
+            rep, x = ddg.ddg_fcg_solve(p, 1e-6, 600, 10)
+            alone.append((rep, x))
+            ddg.ddg_problem_destroy(p)
+        # in the mix: all submitted at once, solved concurrently by the scheduler
+        ddg.ddg_serve_config(ctx, 4)
+        tickets = [ddg.ddg_submit(ctx, mesh.xy, mesh.tri, r, kind, m if kind == ddg.DDG_DDM_GNN else None,
+                                  max_iter=600) for mesh, r, kind in reqs]
+        res = _wait(ddg, ctx, tickets, [mesh.n for mesh, _, _ in reqs])
+        for t, (rep_a, x_a) in zip(tickets, alone):
+            st, rep, x = res[t]
+            assert st == rep_a["status"]
+            assert rep["iterations"] == rep_a["iterations"]
+            assert np.array_equal(x, x_a)
+        stats = ddg.ddg_serve_stats(ctx)
+        assert stats["completed"] == len(reqs) and stats["pending"] == 0 and stats["active"] == 0
+        assert stats["p99_ms"] >= stats["p50_ms"] > 0
+        with pytest.raises(ddg.DdgError):
+            ddg.ddg_poll(ctx, tickets[0], reqs[0][0].n)       # a ticket is collected once
+    finally:
+        ddg.ddg_model_destroy(m)
+        ddg.ddg_destroy(ctx)
+
+
+def test_admission_waits_for_the_hbm_budget():
+    import paper_2402_08296_b300 as ddg
+    budget = 200 << 20
+    ctx = ddg.ddg_create(0, budget)
+    try:
+        meshes = [synth.star_mesh(30000, seed=400 + i) for i in range(5)]
+        tickets = [ddg.ddg_submit(ctx, mesh.xy, mesh.tri, synth.poly_coeffs(400 + i), ddg.DDG_DDM_LU, max_iter=400)
+                   for i, mesh in enumerate(meshes)]
+        peak = 0
+        t0 = time.time()
+        done = {}
+        while len(done) < len(tickets):
+            stats = ddg.ddg_serve_stats(ctx)
+            peak = max(peak, stats["reserved_bytes"])
+            for t, mesh in zip(tickets, meshes):
+                if t not in done:
+                    st, rep, x = ddg.ddg_poll(ctx, t, mesh.n)
+                    if st != ddg.DDG_PENDING:
+                        done[t] = st
+            assert time.time() - t0 < 300
+            time.sleep(0.001)
+        assert all(st == ddg.DDG_OK for st in done.values())
+        assert peak <= budget
+    finally:
+        ddg.ddg_destroy(ctx)
