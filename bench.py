@@ -48,6 +48,15 @@ def args_parse():
     ap.add_argument("--m", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iterations", type=int, default=70,
+                    help="reference arm: preconditioner applications a solve is scaled to (the DDM-GNN "
+                         "iteration count of star100k with the committed weights)")
+    ap.add_argument("--requests", type=int, default=24, help="serve workload: requests in the stream")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve workload: mean arrivals per second")
+    ap.add_argument("--n-min", type=int, default=10_000, help="serve workload: smallest mesh (nodes)")
+    ap.add_argument("--n-max", type=int, default=1_000_000, help="serve workload: largest mesh (nodes)")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve workload: HBM admission budget")
+    ap.add_argument("--max-active", type=int, default=16, help="serve workload: requests in flight at most")
     return ap.parse_args()
 
 
@@ -263,7 +272,7 @@ def run_ours(a, rank, world, local_rank):
                      "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
                      "flops_per_application": flops, "nodes": nodes, "messages": msgs,
                      "avg_application_ms": avg_launch_s * 1e3,
-                     "gnn_schedule": r_gnn[0]["gnn_schedule"],
+                     "gnn_schedule": r_gnn[0]["gnn_schedule"], "gnn_chunk_t": r_gnn[0]["gnn_chunk_t"],
                      "kernel_launches_per_application": r_gnn[0]["local_launches"] // max(1, r_gnn[0]["local_applies"]),
                      "peak_note": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (unit counts and max clock)"},
         "clocks": clk,
@@ -271,39 +280,152 @@ def run_ours(a, rank, world, local_rank):
     return out
 
 
+# ---------------------------------------------------------------- serving
+def run_serve(a, rank, local_rank):
+    """A Poisson stream of independent solves with log-uniform mesh sizes, served by the
+    library's request loop (ddg_submit / ddg_poll), once with DDM-GNN and once with DDM-LU.
+
+    The meshes are generated before the clock starts (they are the requests' inputs); the
+    submitting thread releases each request at its arrival time.  Latency is submit to result.
+    """
+    import torch
+    import paper_2402_08296_b300 as ddg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    stream_reqs = synth.request_stream(a.requests, a.rate, a.n_min, a.n_max, a.seed + 1000 * rank)
+    meshes = [synth.star_mesh(q.n_target, seed=q.seed) for q in stream_reqs]
+    coeffs = [synth.poly_coeffs(q.seed) for q in stream_reqs]
+    W, wkind = load_weights(synth)
+    budget = int(a.budget_gb * (1 << 30))
+
+    def serve(kind):
+        ctx = ddg.ddg_create(local_rank, budget)
+        model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, W) if kind == ddg.DDG_DDM_GNN else None
+        try:
+            ddg.ddg_serve_config(ctx, a.max_active)
+            # warm-up: one small request (context, kernels, schedule tuning of the small class)
+            wm = synth.star_mesh(a.n_min, seed=a.seed + 99991)
+            t = ddg.ddg_submit(ctx, wm.xy, wm.tri, synth.poly_coeffs(a.seed + 99991), kind, model,
+                               rtol=a.tol, max_iter=a.max_iter, m_trunc=a.m)
+            while ddg.ddg_poll(ctx, t)[0] == ddg.DDG_PENDING:
+                time.sleep(0.001)
+            torch.cuda.synchronize()
+            l0 = ddg.ddg_launch_count()
+            clocks = Clocks(local_rank)
+            clocks.start()
+            tickets, lat, reps = [], {}, {}
+            t0 = time.perf_counter()
+            sub_t = {}
+            for q, m, r in zip(stream_reqs, meshes, coeffs):
+                while time.perf_counter() - t0 < q.arrival_s:
+                    time.sleep(0.0002)
+                tk = ddg.ddg_submit(ctx, m.xy, m.tri, r, kind, model, rtol=a.tol, max_iter=a.max_iter, m_trunc=a.m)
+                sub_t[tk] = time.perf_counter()
+                tickets.append((tk, m.n))
+            left = dict(tickets)
+            while left:
+                for tk, n in list(left.items()):
+                    st, rep, _ = ddg.ddg_poll(ctx, tk)
+                    if st != ddg.DDG_PENDING:
+                        lat[tk] = (time.perf_counter() - sub_t[tk]) * 1e3
+                        reps[tk] = (st, rep)
+                        del left[tk]
+                time.sleep(0.0005)
+            wall = time.perf_counter() - t0
+            clk = clocks.stop()
+            stats = ddg.ddg_serve_stats(ctx)
+            launches = ddg.ddg_launch_count() - l0
+        finally:
+            if model is not None:
+                ddg.ddg_model_destroy(model)
+            ddg.ddg_destroy(ctx)
+        ok = [tk for tk, (st, rep) in reps.items() if st == ddg.DDG_OK and rep["true_rel_residual"] <= 1.01 * a.tol]
+        l = np.array([lat[tk] for tk, _ in tickets])
+        return {"solves_per_s": len(ok) / wall, "wall_s": wall, "completed": len(reps), "converged": len(ok),
+                "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99)),
+                "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"],
+                "iterations": [reps[tk][1]["iterations"] for tk, _ in tickets],
+                "nodes": [n for _, n in tickets], "launches": launches, "clocks": clk}
+
+    g = serve(ddg.DDG_DDM_GNN)
+    lu = serve(ddg.DDG_DDM_LU)
+    h2d = sum(m.xy.nbytes + m.tri.nbytes + 72 for m in meshes)
+    d2h = sum(8 * m.n for m in meshes)
+    return {"metric": METRIC, "value": g["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": a.requests, "warmup": 1, "ms_per_step": 1e3 * g["wall_s"] / a.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 GNN / f64 Krylov",
+            "data": "synthetic",
+            "config": {"workload": "serve", "requests": a.requests, "rate_per_s": a.rate,
+                       "n_min": a.n_min, "n_max": a.n_max, "budget_gb": a.budget_gb, "max_active": a.max_active,
+                       "kbar": KBAR, "d": D, "tol": a.tol, "fcg_m": a.m, "weights": wkind,
+                       "l2": "inputs of the stream exceed L2", "parallelism": "replicas x1"},
+            "gnn": g, "lu": lu,
+            "e2e": {"value": g["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d // a.requests,
+                    "d2h_bytes_per_step": d2h // a.requests,
+                    "note": "the serving path is end to end: host mesh in, host solution out"},
+            "gpu_launches": g["launches"], "clocks": g["clocks"]}
+
+
 # ---------------------------------------------------------------- CPU oracle
+def _oracle_worker_init():
+    from threadpoolctl import threadpool_limits
+    threadpool_limits(1)
+
+
+def _oracle_dss(job):
+    from oracle import dss
+    g_xy, n_int, src, dst, c, W, hbar = job
+    t = time.perf_counter()
+    dss.forward(g_xy, n_int, src, dst, c, W, KBAR, D, ALPHA, hbar)
+    return time.perf_counter() - t
+
+
 def oracle_sample(a, budget_s: float):
     """Time the oracle on a bounded sample of the workload and scale it to one solve.
 
-    Sample: assembly + decomposition of the full mesh, then DSS inferences on
-    as many subdomains as fit the budget, scaled to all K subdomains and to
-    the iteration count given (one preconditioner application per iteration).
+    Sample: assembly + decomposition of the full mesh (one process, as the oracle is
+    written), then FP64 DSS inferences of whole subdomains spread over a pool of one
+    single-threaded worker per host core (spawned, so no GPU state is inherited), as
+    many rounds of subdomains as fit the budget, scaled to all K subdomains and to the
+    iteration count given (one preconditioner application per iteration).
     """
+    import multiprocessing as mp
     import synth
-    from oracle import ddm, dss, fem, partition as pt
+    from oracle import fem, partition as pt
 
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     w = synth.workload(a.workload, a.seed)
     W, _ = load_weights(synth)
-    t0 = time.perf_counter()
-    P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
-    Dd = pt.decompose(P, w.K, w.overlap)
-    adj = pt.mesh_adjacency(P.n, P.tri)
-    hbar = pt.mean_edge_length(P.xy, P.tri)
-    t_setup = time.perf_counter() - t0
-    r = P.b
-    done, t_dss = 0, 0.0
-    for i, S in enumerate(Dd.sets):
-        t1 = time.perf_counter()
-        g = pt.local_graph(P, S, adj)
-        s = np.linalg.norm(r[S])
-        dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / s, W, KBAR, D, ALPHA, hbar)
-        t_dss += time.perf_counter() - t1
-        done += 1
-        if t_setup + t_dss > budget_s:
-            break
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init)
+    try:
+        pool.map(abs, range(cores))   # start every worker before the clock
+        t0 = time.perf_counter()
+        P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
+        Dd = pt.decompose(P, w.K, w.overlap)
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        t_setup = time.perf_counter() - t0
+        r = P.b
+        done, t_dss = 0, 0.0
+        while done < len(Dd.sets) and t_setup + t_dss < budget_s:
+            jobs = []
+            for S in Dd.sets[done: done + cores]:
+                t1 = time.perf_counter()
+                g = pt.local_graph(P, S, adj)
+                t_setup += time.perf_counter() - t1
+                s = np.linalg.norm(r[S])
+                jobs.append((g.xy, g.n_int, g.src, g.dst, r[S] / s, W, hbar))
+            t1 = time.perf_counter()
+            pool.map(_oracle_dss, jobs, chunksize=1)
+            t_dss += time.perf_counter() - t1
+            done += len(jobs)
+    finally:
+        pool.terminate()
+        pool.join()
     per_apply = t_dss / done * w.K
     return {"t_setup_s": t_setup, "per_precond_s": per_apply, "subdomains_sampled": done, "K": w.K,
-            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+            "cores": cores}
 
 
 def run_reference(a, rank):
@@ -313,7 +435,7 @@ def run_reference(a, rank):
     samp = None
     for _ in range(a.warmup + a.steps):
         samp = oracle_sample(a, a.cpu_seconds / max(1, a.warmup + a.steps))
-        times.append(samp["t_setup_s"] + a.max_iter_ref * samp["per_precond_s"])
+        times.append(samp["t_setup_s"] + a.ref_iterations * samp["per_precond_s"])
     t = np.array(times[a.warmup:])
     v = 1.0 / float(t.mean())
     return {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
@@ -321,9 +443,9 @@ def run_reference(a, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": a.workload, "kbar": KBAR, "d": D, "tol": a.tol},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": samp["cores"], "kind": "oracle",
-                             "sample": f"assembly + decomposition + DSS on {samp['subdomains_sampled']} of "
-                                       f"{samp['K']} subdomains, scaled to {a.max_iter_ref} preconditioner "
-                                       f"applications"},
+                             "sample": f"assembly + decomposition + FP64 DSS on {samp['subdomains_sampled']} of "
+                                       f"{samp['K']} subdomains ({samp['cores']} single-threaded worker "
+                                       f"processes), scaled to {a.ref_iterations} preconditioner applications"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -332,10 +454,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    a.max_iter_ref = 50
     if a.impl == "reference":
         out = run_reference(a, rank)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if a.workload == "serve":
+        out = run_serve(a, rank, local_rank)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     out = run_ours(a, rank, world, local_rank)
@@ -347,8 +473,8 @@ def main():
         t = s["t_setup_s"] + its * s["per_precond_s"]
         out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": s["cores"], "kind": "oracle",
                                "sample": f"assembly + decomposition + FP64 DSS on {s['subdomains_sampled']} of "
-                                         f"{s['K']} subdomains, scaled to {its} preconditioner applications "
-                                         f"(the GPU's iteration count)"}
+                                         f"{s['K']} subdomains ({s['cores']} single-threaded worker processes), "
+                                         f"scaled to {its} preconditioner applications (the GPU's iteration count)"}
     print(json.dumps(out), flush=True)
 
 

@@ -73,7 +73,9 @@ typedef struct ddg_solve_report {
     int32_t local_launches;    /* kernel launches of the local solves inside the loop */
     int32_t launches;          /* all kernel launches of the library inside the loop */
     int32_t local_applies;     /* local-solve applications (one per iteration) */
-    int32_t gnn_schedule;      /* 0: one launch per application, 1: one launch per message-passing block */
+    int32_t gnn_schedule;      /* 0: one launch per application, 1: one launch per message-passing block,
+                                  2: as 1 with the graphs cut into chunks of at most 2 * gnn_chunk_t nodes */
+    int32_t gnn_chunk_t;       /* threads per CTA of schedule 2 (0 otherwise) */
 } ddg_solve_report;
 
 /* ---- context --------------------------------------------------------- */

@@ -53,7 +53,7 @@ class ddg_solve_report(ctypes.Structure):
     _fields_ = [("status", _i32), ("iterations", _i32), ("rel_residual", _f64),
                 ("true_rel_residual", _f64), ("solve_ms", _f64), ("precond_ms", _f64),
                 ("local_ms", _f64), ("local_launches", _i32), ("launches", _i32),
-                ("local_applies", _i32), ("gnn_schedule", _i32)]
+                ("local_applies", _i32), ("gnn_schedule", _i32), ("gnn_chunk_t", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

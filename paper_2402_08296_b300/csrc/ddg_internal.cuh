@@ -77,9 +77,10 @@ struct ddg_ctx {
     ddg::Server *server = nullptr;  // started by the first ddg_submit
     std::mutex server_mu;
     std::mutex tune_mu;             // guards `tuned` (set-up may run on the scheduler thread)
-    // GNN schedule chosen by the autotuner, cached per decomposition shape (K, graph nodes, largest graph)
+    // GNN schedule chosen by the autotuner, cached per decomposition shape class: K in quarter
+    // octaves, mean graph size in steps of 64 nodes, largest graph in steps of 128 nodes
     struct Tuned {
-        long long K, nodes, max_loc;
+        long long K, nodes, max_loc;  // the three classes
         int sched, T;
     };
     std::vector<Tuned> tuned;

@@ -194,7 +194,8 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 // per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
 // the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256).
 // DDG_GNN_SCHEDULE = 0, 1, 2 (and DDG_GNN_CHUNK_T = 128/192/256) forces one.
-// The choice is cached in the context per decomposition shape.
+// The choice is cached in the context per decomposition shape class, so a stream
+// of requests of similar sizes tunes once.
 int32_t dss_autotune(ddg_problem *p) {
     const char *env = getenv("DDG_GNN_SCHEDULE");
     const char *envT = getenv("DDG_GNN_CHUNK_T");
@@ -203,12 +204,15 @@ int32_t dss_autotune(ddg_problem *p) {
         if (p->dss_sched == 2) DDG_TRY(chunk_build(p, envT ? atoi(envT) : 192));
         return DDG_OK;
     }
+    const long long cls_K = (long long)std::floor(4.0 * std::log2((double)p->K));
+    const long long cls_n = p->sum_loc / ((long long)p->K * 64);
+    const long long cls_m = p->max_loc / 128;
     {
         int cached = -1, cachedT = 0;
         {
             std::lock_guard<std::mutex> lock(p->ctx->tune_mu);
             for (const auto &t : p->ctx->tuned)
-                if (t.K == p->K && t.nodes == p->sum_loc && t.max_loc == p->max_loc) {
+                if (t.K == cls_K && t.nodes == cls_n && t.max_loc == cls_m) {
                     cached = t.sched;
                     cachedT = t.T;
                 }
@@ -252,7 +256,7 @@ int32_t dss_autotune(ddg_problem *p) {
     }
     {
         std::lock_guard<std::mutex> lock(p->ctx->tune_mu);
-        p->ctx->tuned.push_back({(long long)p->K, p->sum_loc, (long long)p->max_loc, pick, pickT});
+        p->ctx->tuned.push_back({cls_K, cls_n, cls_m, pick, pickT});
     }
     return check_status(p, "GNN schedule selection");
 }
@@ -685,6 +689,7 @@ struct FcgRun {
         rp.launches = launches;
         rp.local_applies = loc_applies;
         rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
+        rp.gnn_chunk_t = (p->kind == DDG_DDM_GNN && p->dss_sched == 2) ? p->chunk.T : 0;
         rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
         if (rep) *rep = rp;
         release();

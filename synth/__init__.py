@@ -25,7 +25,7 @@ from .mesh import square_mesh, star_mesh, Mesh
 
 __all__ = [
     "rng", "Mesh", "square_mesh", "star_mesh", "poly_coeffs", "dss_weights",
-    "residual_vector", "n_weights_per_block", "workload",
+    "residual_vector", "n_weights_per_block", "workload", "request_stream",
 ]
 
 
@@ -110,3 +110,27 @@ def workload(name: str, seed: int = 0) -> Workload:
     n_free_est = m.n - m.n_boundary_ring
     K = max(1, int(round(n_free_est / 1000.0)))
     return Workload(name, m, coeffs, K, 2)
+
+
+@dataclass
+class Request:
+    arrival_s: float      # seconds after the stream starts
+    n_target: int         # requested mesh size (nodes)
+    seed: int             # seed of its star domain, mesh jitter and f, g coefficients
+
+
+def request_stream(n_requests: int, rate_per_s: float, n_min: int, n_max: int, seed: int) -> list[Request]:
+    """A Poisson-process stream of independent solves with log-uniform mesh sizes.
+
+    Inter-arrival gaps are exponential with mean ``1 / rate_per_s`` (inverse
+    transform of U[0,1)); sizes are ``exp(U(log n_min, log n_max))``; request
+    ``i`` gets the seed ``seed * 1_000_003 + 7919 * (i + 1)`` for its domain
+    and data.
+    """
+    u = rng.uniform(seed, rng.TAG_REQUESTS, 2 * n_requests)
+    t, out = 0.0, []
+    for i in range(n_requests):
+        t += -math.log1p(-u[2 * i]) / rate_per_s
+        n = int(round(math.exp(math.log(n_min) + (math.log(n_max) - math.log(n_min)) * u[2 * i + 1])))
+        out.append(Request(t, n, seed * 1_000_003 + 7919 * (i + 1)))
+    return out

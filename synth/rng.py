@@ -19,6 +19,7 @@ TAG_WEIGHTS = 2
 TAG_VECTOR = 3
 TAG_MESH_JITTER = 4
 TAG_STAR_RADII = 5
+TAG_REQUESTS = 6
 
 
 def mix(z: np.ndarray) -> np.ndarray:
