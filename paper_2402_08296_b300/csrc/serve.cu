@@ -22,6 +22,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 
 namespace ddg {
@@ -55,6 +56,7 @@ struct Server {
     std::deque<ServeRequest *> pending;
     std::vector<ServeRequest *> active;
     std::map<uint64_t, ServeRequest *> finished;
+    std::set<uint64_t> live;  // tickets submitted and not yet collected
     bool stop = false;
     uint64_t next_ticket = 1;
     int max_active = 64;
@@ -242,6 +244,7 @@ int32_t ddg_submit(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n_tri,
     Server *S = server_get(c);
     std::lock_guard<std::mutex> lock(S->mu);
     q->ticket = S->next_ticket++;
+    S->live.insert(q->ticket);
     if (S->t_first_submit < 0.0) S->t_first_submit = q->t_submit;
     S->pending.push_back(q);
     *ticket = q->ticket;
@@ -261,8 +264,7 @@ int32_t ddg_poll(ddg_ctx *c, uint64_t ticket, ddg_solve_report *report, double *
         std::lock_guard<std::mutex> lock(S->mu);
         auto it = S->finished.find(ticket);
         if (it == S->finished.end()) {
-            bool known = ticket > 0 && ticket < S->next_ticket;
-            if (!known) {
+            if (!S->live.count(ticket)) {
                 set_error("ddg_poll: unknown or already collected ticket");
                 return DDG_INVALID_ARG;
             }
@@ -270,6 +272,7 @@ int32_t ddg_poll(ddg_ctx *c, uint64_t ticket, ddg_solve_report *report, double *
         }
         q = it->second;
         S->finished.erase(it);
+        S->live.erase(ticket);
     }
     if (report) *report = q->rep;
     if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), sizeof(double) * q->x.size());
