@@ -13,6 +13,12 @@ host buffers (mesh upload and solution download inside the timed region).
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs an independent replica (the solver does not
 shard across GPUs); rank 0 prints one JSON line.
+
+Other workloads: ``--workload star1m`` (or any ``starN``) for the same measurement
+on another mesh; ``--workload serve`` for a Poisson stream of requests through the
+library's request loop (``--requests --rate --n-min --n-max --budget-gb``);
+``--workload variants[:starN]`` for the paper's variants (sub-mesh size, overlap,
+one- vs two-level, kbar, tolerance) as a table of rows.
 """
 from __future__ import annotations
 
@@ -280,6 +286,69 @@ def run_ours(a, rank, world, local_rank):
     return out
 
 
+# ---------------------------------------------------------------- paper variants
+def run_variants(a, local_rank):
+    """Section V-B/V-C variants on one mesh: sub-mesh size N_s (500, 1000, 2000), overlap
+    (2, 4), one- vs two-level, kbar (30, and 10 when its weights exist), tolerance (1e-6, 1e-3),
+    for DDM-GNN and DDM-LU.  Each row: set-up + solve timed with CUDA events, median of steps."""
+    import torch
+    import paper_2402_08296_b300 as ddg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    base = a.workload_variants
+    w = synth.workload(base, a.seed)
+    ctx = ddg.ddg_create(local_rank)
+    stream = torch.cuda.ExternalStream(ddg.ddg_get_stream(ctx), device=f"cuda:{local_rank}")
+    W30, kind30 = load_weights(synth)
+    models = {30: (ddg.ddg_model_create(ctx, 30, D, ALPHA, W30), kind30)}
+    w10 = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k10_d10.npy")
+    if os.path.exists(w10):
+        models[10] = (ddg.ddg_model_create(ctx, 10, D, ALPHA, np.load(w10).astype(np.float32)), "trained")
+    p = ddg.ddg_mesh_upload(ctx, w.mesh.xy, w.mesh.tri)
+    ddg.ddg_assemble_poly(p, w.coeffs)
+    n_free = ddg.ddg_problem_info(p)["n_free"]
+    rows = []
+    configs = [("two-level", 1000, 2, ddg.DDG_COARSE), ("one-level", 1000, 2, 0), ("two-level", 1000, 4, ddg.DDG_COARSE),
+               ("two-level", 500, 2, ddg.DDG_COARSE), ("two-level", 2000, 2, ddg.DDG_COARSE)]
+    for tol in (1e-6, 1e-3):
+        for level, ns, delta, flags in configs:
+            K = max(1, int(round(n_free / ns)))
+            for kind, kbar in [(ddg.DDG_DDM_LU, None)] + [(ddg.DDG_DDM_GNN, kb) for kb in sorted(models, reverse=True)]:
+                if kbar == 10 and (ns != 1000 or delta != 2 or level != "two-level"):
+                    continue
+                model = models[kbar][0] if kbar else None
+                times, its, res = [], [], []
+                for rep in range(a.steps + 1):
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ddg.ddg_partition(p, K, delta)
+                    ddg.ddg_setup_precond(p, kind, model, flags)
+                    r, _ = ddg.ddg_fcg_solve(p, tol, a.max_iter, a.m, want_x=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep > 0:
+                        times.append(e0.elapsed_time(e1))
+                        its.append(r["iterations"])
+                        res.append(r["true_rel_residual"])
+                ms = float(np.median(times))
+                rows.append({"precond": "DDM-GNN" if kbar else "DDM-LU", "kbar": kbar, "level": level, "N_s": ns,
+                             "K": K, "overlap": delta, "tol": tol, "iterations": int(np.median(its)),
+                             "true_rel_residual": float(np.max(res)), "ms": ms, "solves_per_s": 1e3 / ms})
+    for m, _ in models.values():
+        ddg.ddg_model_destroy(m)
+    ddg.ddg_problem_destroy(p)
+    ddg.ddg_destroy(ctx)
+    head = next(r for r in rows if r["precond"] == "DDM-GNN" and r["tol"] == 1e-6)
+    return {"metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 GNN / f64 Krylov", "data": "synthetic",
+            "config": {"workload": "variants", "mesh": base, "n_free": n_free, "fcg_m": a.m,
+                       "weights": {str(k): v[1] for k, v in models.items()}},
+            "rows": rows}
+
+
 # ---------------------------------------------------------------- serving
 def run_serve(a, rank, local_rank):
     """A Poisson stream of independent solves with log-uniform mesh sizes, served by the
@@ -368,11 +437,6 @@ def run_serve(a, rank, local_rank):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def _oracle_worker_init():
-    from threadpoolctl import threadpool_limits
-    threadpool_limits(1)
-
-
 def _oracle_dss(job):
     from oracle import dss
     g_xy, n_int, src, dst, c, W, hbar = job
@@ -397,7 +461,17 @@ def oracle_sample(a, budget_s: float):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     w = synth.workload(a.workload, a.seed)
     W, _ = load_weights(synth)
-    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init)
+    # single-threaded BLAS in every worker: the variables are read when the child imports numpy
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({v: "1" for v in saved})
+    try:
+        pool = mp.get_context("spawn").Pool(cores)
+    finally:
+        for v, x in saved.items():
+            if x is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = x
     try:
         pool.map(abs, range(cores))   # start every worker before the clock
         t0 = time.perf_counter()
@@ -457,6 +531,12 @@ def main():
     if a.impl == "reference":
         out = run_reference(a, rank)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if a.workload.startswith("variants"):
+        a.workload_variants = a.workload.split(":", 1)[1] if ":" in a.workload else "star100k"
+        out = run_variants(a, local_rank)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     if a.workload == "serve":

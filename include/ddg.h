@@ -59,7 +59,9 @@ enum ddg_precond_kind { DDG_NONE = 0, DDG_DDM_LU = 1, DDG_DDM_GNN = 2 };
 
 enum ddg_precond_flags {
     DDG_COARSE = 1u,      /* add the Nicolaides coarse correction (two-level, Eq. 7) */
-    DDG_POU_PROLONG = 2u  /* glue local corrections with partition-of-unity weights instead of R_i^T */
+    DDG_POU_PROLONG = 2u, /* glue local corrections with partition-of-unity weights instead of R_i^T */
+    DDG_BF16_WEIGHTS = 4u /* DDM-GNN: run with the model's weights rounded to bfloat16 (nearest, ties to even);
+                             latents and arithmetic stay FP32.  Not in the paper: a storage-precision variant */
 };
 
 typedef struct ddg_solve_report {
@@ -166,6 +168,12 @@ int32_t ddg_model_create(ddg_ctx *ctx, int32_t kbar, int32_t d, float alpha, con
 int32_t ddg_model_destroy(ddg_model *m);
 int32_t ddg_model_get_weights(ddg_model *m, float *w, size_t n_w);
 
+/* Replace the model's weights by w[n_w] (host, copied; flat layout of
+ * ddg_model_create).  Problems set up with this model see the new weights at
+ * their next GNN launch; the Adam moments of ddg_train_local_model are kept.
+ * Errors: DDG_INVALID_ARG (n_w differs from the model's). */
+int32_t ddg_model_set_weights(ddg_model *m, const float *w, size_t n_w);
+
 /* Training of the DSS local solver (Section III-B, Eq. 23; optimiser of
  * Section IV-B) on the local problems of problem p's own decomposition
  * (Section IV-A): p is set up with DDG_DDM_LU (it stays so), preconditioned
@@ -212,9 +220,11 @@ int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, c
 /* Build the preconditioner of the given kind on the current partition:
  * DDG_DDM_LU factorises every R_i A R_i^T (banded FP64 Cholesky);
  * DDG_DDM_GNN uses `model` (kept by reference; it must outlive its use).
- * flags: DDG_COARSE, DDG_POU_PROLONG.  Errors: DDG_INVALID_ARG (no
- * partition, missing model), DDG_TOO_LARGE (a local graph beyond the GNN
- * kernel's 2048 nodes), DDG_OOM. */
+ * flags: DDG_COARSE, DDG_POU_PROLONG, DDG_BF16_WEIGHTS.  The GNN schedule
+ * is tuned here (timed on the right-hand side, cached per decomposition
+ * shape class); local graphs of more than 2,048 nodes run on the chunked
+ * schedules.  Errors: DDG_INVALID_ARG (no partition, missing model),
+ * DDG_TOO_LARGE (a local graph beyond 65,535 nodes), DDG_OOM. */
 int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, uint32_t flags);
 
 /* z = M^-1 r for device vectors r_dev, z_dev of n_free FP64 (Eqs. 13-16 for

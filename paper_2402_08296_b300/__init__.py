@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR", -4: "NO
                 -5: "BREAKDOWN", -8: "PENDING", -9: "BAD_MESH", -10: "TOO_LARGE"}
 
 DDG_NONE, DDG_DDM_LU, DDG_DDM_GNN = 0, 1, 2
-DDG_COARSE, DDG_POU_PROLONG = 1, 2
+DDG_COARSE, DDG_POU_PROLONG, DDG_BF16_WEIGHTS = 1, 2, 4
 
 _p = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -105,6 +105,7 @@ _SIGS = {
     "ddg_model_create": [_p, _i32, _i32, _f32, _p, _sz, _u64, ctypes.POINTER(_p)],
     "ddg_model_destroy": [_p],
     "ddg_model_get_weights": [_p, _p, _sz],
+    "ddg_model_set_weights": [_p, _p, _sz],
     "ddg_setup_precond": [_p, _i32, _p, ctypes.c_uint32],
     "ddg_precondition": [_p, _p, _p, _p],
     "ddg_local_corrections": [_p, _p, _p, _p, _p],
@@ -315,6 +316,11 @@ def ddg_model_get_weights(m, n_w: int) -> np.ndarray:
     return w
 
 
+def ddg_model_set_weights(m, w) -> None:
+    w_a, w_p = _host(w, np.float32)
+    _check(lib.ddg_model_set_weights(m, w_p, ctypes.c_size_t(w_a.size)), "ddg_model_set_weights")
+
+
 def ddg_setup_precond(p, kind: int, model=None, flags: int = DDG_COARSE) -> None:
     _check(lib.ddg_setup_precond(p, kind, model, flags), "ddg_setup_precond")
 
@@ -405,3 +411,37 @@ def ddg_serve_stats(ctx) -> dict:
     out = ddg_serve_summary()
     _check(lib.ddg_serve_stats(ctx, ctypes.byref(out)), "ddg_serve_stats")
     return out.as_dict()
+
+
+_LOSS_FN = None
+
+
+def dss_residual_loss(w, p, m, r_dev, graphs):
+    """The training loss of Eq. 23 as a differentiable PyTorch function of the flat weights.
+
+    Sets model m's weights to the float32 tensor ``w``, runs the library's forward kernel
+    (saving every block's latents) and its hand-written backward kernel on the local graphs
+    ``graphs`` of problem p with global residual ``r_dev``, and returns the loss as a 0-d
+    FP64 tensor whose ``backward`` yields the gradient those kernels computed (a
+    torch.autograd.Function; no PyTorch arithmetic is involved).
+    """
+    global _LOSS_FN
+    if _LOSS_FN is None:
+        import torch
+
+        class _DssResidualLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, w, p, m, r_dev, graphs):
+                wh = w.detach().to("cpu", torch.float32).contiguous().numpy()
+                ddg_model_set_weights(m, wh)
+                loss, grad = ddg_train_loss_grad(p, m, r_dev, graphs, wh.size)
+                ctx.save_for_backward(torch.as_tensor(grad).to(w.device))
+                return torch.tensor(loss, dtype=torch.float64, device=w.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                (grad,) = ctx.saved_tensors
+                return g.to(grad.dtype) * grad, None, None, None, None
+
+        _LOSS_FN = _DssResidualLoss
+    return _LOSS_FN.apply(w, p, m, r_dev, graphs)

@@ -300,6 +300,17 @@ int32_t ddg_model_get_weights(ddg_model *m, float *w, size_t n_w) {
     return DDG_OK;
 }
 
+int32_t ddg_model_set_weights(ddg_model *m, const float *w, size_t n_w) {
+    API_BEGIN;
+    REQUIRE(m && w && n_w == m->n_w, "bad arguments");
+    DDG_TRY(use_device(m->ctx));
+    DDG_CU(cudaMemcpy(m->w, w, sizeof(float) * n_w, cudaMemcpyHostToDevice));
+    DDG_TRY(model_host_layouts(m));
+    DDG_CU(cudaMemcpy(m->packed, m->packed_host.data(), sizeof(float) * m->packed_host.size(),
+                      cudaMemcpyHostToDevice));
+    return DDG_OK;
+}
+
 // ------------------------------------------------------------------ preconditioner and solver
 int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, uint32_t flags) {
     API_BEGIN;
@@ -326,6 +337,7 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
         DDG_TRY(lu_build(p));
     } else {
         DDG_TRY(dss_check_capacity(p));
+        DDG_TRY(dss_select_weights(p, (flags & DDG_BF16_WEIGHTS) != 0));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_D * p->sum_loc));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, (size_t)DSS_D * p->sum_loc));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_c, p->sum_loc));

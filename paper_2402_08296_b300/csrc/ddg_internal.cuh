@@ -95,6 +95,7 @@ struct ddg_model {
     float *packed = nullptr;  // per-block padded layout read by the GNN kernel (device)
     size_t packed_per_block = 0;
     std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
+    std::vector<float> fused_host;   // composed per-block layout of the fused GNN kernel (kernel parameters)
     float *adam_m = nullptr, *adam_v = nullptr;  // Adam moments, kept across training calls
     long long adam_t = 0;
     ddg::Allocs allocs;
@@ -103,6 +104,9 @@ struct ddg_model {
 // chunked GNN schedule: graphs cut into chunks of at most 2 * T nodes (see dss.cu)
 struct ChunkPlan {
     int T = 0, nchunks = 0, max_need = 0;
+    bool global = false;  // schedule 3: chunks are ranges of the concatenated graphs' nodes, sized to fill
+                          // the GPU evenly; own nodes sorted by message count, neighbour kind in bit 15
+    int *gid = nullptr;   // global: graph of every local node (sum_loc)
     int *c_graph = nullptr, *c_n0 = nullptr, *c_own = nullptr, *c_need_off = nullptr, *c_need_n = nullptr;
     int *need = nullptr, *c_adj_off = nullptr, *adj_ptr = nullptr, *c_adj_base = nullptr;
     uint16_t *adj = nullptr;
@@ -170,7 +174,13 @@ struct ddg_problem {
     double *lu_band = nullptr;
     int lu_kmax = 0;
     double *s = nullptr, *y = nullptr, *wc = nullptr, *corr = nullptr;
-    int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block
+    // GNN weights in use: the model's, or (DDG_BF16_WEIGHTS) this problem's copies rounded to bfloat16
+    bool w_bf16 = false;
+    float *bf16_packed_dev = nullptr;
+    std::vector<float> bf16_packed_host, bf16_fused_host;
+    bool dss_whole_graph = true;  // every local graph fits one CTA (schedules 0 and 1 allowed)
+    int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block,
+                                // 3 chunked per block with composed weights and packed two-lane FP32
     float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedules 1, 2)
     float *dss_h2 = nullptr;    // second latent buffer (schedule 2)
     ChunkPlan chunk;
@@ -217,10 +227,13 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
                       double *corr_out, double *s_out);
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s);
 int32_t model_pack(ddg_model *m);
+int32_t model_host_layouts(ddg_model *m);
+int32_t dss_select_weights(ddg_problem *p, bool bf16);  // rebuilds packed_host and fused_host from the device flat weights
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
 int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
 int32_t chunk_build(ddg_problem *p, int T);
+int32_t chunk_build_global(ddg_problem *p, int T);
 void chunk_free(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include "dss_layout.cuh"
 
 #include <climits>
+#include <cstring>
 
 #include <cmath>
 
@@ -52,14 +53,69 @@ static FlatOffsets flat_offsets(int d) {
     return f;
 }
 
-int32_t model_pack(ddg_model *m) {
-    // host-side repacking of the flat weights into the kernel's padded, transposed layout
-    const int kbar = m->kbar, d = m->d;
+// one block of the fused layout (see dss_layout.cuh) from one block of flat weights;
+// compositions are formed in FP64 and rounded once
+static void fuse_block(const float *w, const FlatOffsets &fo, float alpha, float *o) {
+    const int in1 = 2 * D + 3, inp = 3 * D + 1;
+    const float *Wo1 = w + fo.phi[0][0], *bo1 = w + fo.phi[0][1], *Wo2 = w + fo.phi[0][2], *bo2 = w + fo.phi[0][3];
+    const float *Wi1 = w + fo.phi[1][0], *bi1 = w + fo.phi[1][1], *Wi2 = w + fo.phi[1][2], *bi2 = w + fo.phi[1][3];
+    const float *P1 = w + fo.psi[0], *pb1 = w + fo.psi[1], *P2 = w + fo.psi[2], *pb2 = w + fo.psi[3];
+    const float *dW1 = w + fo.dec[0], *db1 = w + fo.dec[1], *dW2 = w + fo.dec[2], *db2 = w + fo.dec[3];
+    for (int i = 0; i < D; ++i)
+        for (int m = 0; m < D / 2; ++m)
+            for (int t = 0; t < 4; ++t)
+                o[F_HB + i * 2 * D + 4 * m + t] =
+                    t < 2 ? Wo1[(2 * m + t) * in1 + D + i] : Wi1[(2 * m + t - 2) * in1 + D + i];
+    for (int i = 0; i < D; ++i)
+        for (int q = 0; q < D; ++q) {
+            o[F_HA + i * 3 * D + q] = Wo1[q * in1 + i];
+            o[F_HA + i * 3 * D + D + q] = Wi1[q * in1 + i];
+            o[F_HA + i * 3 * D + 2 * D + q] = P1[q * inp + i];
+        }
+    for (int q = 0; q < D; ++q) {
+        o[F_BA + q] = bo1[q];
+        o[F_BA + D + q] = bi1[q];
+        o[F_BA + 2 * D + q] = pb1[q];
+        for (int c = 0; c < 3; ++c) {
+            o[F_WEO + c * D + q] = Wo1[q * in1 + 2 * D + c];
+            o[F_WEI + c * D + q] = (c < 2 ? -1.f : 1.f) * Wi1[q * in1 + 2 * D + c];
+        }
+        o[F_VC + q] = P1[q * inp + D];
+        double vo = 0.0, vi = 0.0;
+        for (int t = 0; t < D; ++t) {
+            vo += (double)P1[q * inp + D + 1 + t] * bo2[t];
+            vi += (double)P1[q * inp + 2 * D + 1 + t] * bi2[t];
+        }
+        o[F_VO + q] = (float)vo;
+        o[F_VI + q] = (float)vi;
+        for (int mi = 0; mi < D; ++mi) {
+            double so = 0.0, si = 0.0;
+            for (int t = 0; t < D; ++t) {
+                so += (double)P1[q * inp + D + 1 + t] * Wo2[t * D + mi];
+                si += (double)P1[q * inp + 2 * D + 1 + t] * Wi2[t * D + mi];
+            }
+            o[F_MO + mi * D + q] = (float)so;
+            o[F_MI + mi * D + q] = (float)si;
+            o[F_P2 + mi * D + q] = (float)((double)alpha * P2[q * D + mi]);
+            o[F_DW1 + mi * D + q] = dW1[q * D + mi];
+        }
+        o[F_PB2 + q] = (float)((double)alpha * pb2[q]);
+        o[F_DB1 + q] = db1[q];
+        o[F_DW2 + q] = dW2[q];
+    }
+    o[F_DB2] = db2[0];
+    o[F_DB2 + 1] = 0.f;
+}
+
+// both host layouts (padded per-block, composed per-block) from flat weights
+static void host_layouts(const std::vector<float> &flat, int kbar, int d, float alpha, std::vector<float> &pk,
+                         std::vector<float> &fused) {
     FlatOffsets fo = flat_offsets(d);
-    std::vector<float> flat(m->n_w), pk((size_t)kbar * BLOCK_FLOATS, 0.f);
-    DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
+    pk.assign((size_t)kbar * BLOCK_FLOATS, 0.f);
+    fused.assign((size_t)kbar * F_FLOATS, 0.f);
     for (int k = 0; k < kbar; ++k) {
         const float *w = flat.data() + (size_t)k * fo.size;
+        fuse_block(w, fo, alpha, fused.data() + (size_t)k * F_FLOATS);
         float *o = pk.data() + (size_t)k * BLOCK_FLOATS;
         for (int mm = 0; mm < 2; ++mm) {
             float *ph = o + (mm == 0 ? OFF_OUT : OFF_IN);
@@ -94,10 +150,58 @@ int32_t model_pack(ddg_model *m) {
         }
         de[DEC_B2] = db2[0];
     }
-    DDG_TRY(dalloc(m->ctx, m->allocs, &m->packed, pk.size()));
-    DDG_CU(cudaMemcpy(m->packed, pk.data(), sizeof(float) * pk.size(), cudaMemcpyHostToDevice));
-    m->packed_host = pk;
+}
+
+int32_t model_host_layouts(ddg_model *m) {
+    std::vector<float> flat(m->n_w);
+    DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
+    host_layouts(flat, m->kbar, m->d, m->alpha, m->packed_host, m->fused_host);
+    return DDG_OK;
+}
+
+int32_t model_pack(ddg_model *m) {
+    DDG_TRY(model_host_layouts(m));
+    DDG_TRY(dalloc(m->ctx, m->allocs, &m->packed, m->packed_host.size()));
+    DDG_CU(cudaMemcpy(m->packed, m->packed_host.data(), sizeof(float) * m->packed_host.size(),
+                      cudaMemcpyHostToDevice));
     m->packed_per_block = BLOCK_FLOATS;
+    return DDG_OK;
+}
+
+// round to the nearest bfloat16, ties to even (NaN stays NaN)
+static float round_bf16(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7f800000u) == 0x7f800000u && (b & 0x007fffffu)) return x;
+    b = (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+// the weights a problem's GNN launches read (resolved at launch, so retraining the model is seen)
+static const float *w_packed_dev(const ddg_problem *p) { return p->w_bf16 ? p->bf16_packed_dev : p->model->packed; }
+static const float *w_packed_host(const ddg_problem *p) {
+    return p->w_bf16 ? p->bf16_packed_host.data() : p->model->packed_host.data();
+}
+static const float *w_fused_host(const ddg_problem *p) {
+    return p->w_bf16 ? p->bf16_fused_host.data() : p->model->fused_host.data();
+}
+
+int32_t dss_select_weights(ddg_problem *p, bool bf16) {
+    const ddg_model *m = p->model;
+    p->w_bf16 = bf16;
+    p->bf16_packed_dev = nullptr;
+    if (!bf16) return DDG_OK;
+    std::vector<float> flat(m->n_w);
+    DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
+    for (float &x : flat) x = round_bf16(x);
+    host_layouts(flat, m->kbar, m->d, m->alpha, p->bf16_packed_host, p->bf16_fused_host);
+    float *dev = nullptr;
+    DDG_TRY(dalloc(p->ctx, p->a_pre, &dev, p->bf16_packed_host.size()));
+    DDG_CU(cudaMemcpy(dev, p->bf16_packed_host.data(), sizeof(float) * p->bf16_packed_host.size(),
+                      cudaMemcpyHostToDevice));
+    p->bf16_packed_dev = dev;
     return DDG_OK;
 }
 
@@ -535,6 +639,7 @@ struct ChunkArgs {
     const uint16_t *adj;                    // chunk-local neighbour ids
     const int *c_adj_base;                  // per chunk: start of its slice in adj
     const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
+    const int *gid;                         // global plans: graph of every local node
     const float2 *loc_xy;
     const double *r, *s;
     double *corr;
@@ -677,6 +782,365 @@ __global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid
     }
 }
 
+// ---------------------------------------------------------------- fused global-chunk schedule
+// Schedule 3.  Chunks are equal ranges of the concatenated graphs' nodes (a chunk
+// may hold the end of one graph and the start of the next), as many as fill the
+// SMs' resident CTAs a whole number of times, so every SM gets the same work in
+// every block.  Own nodes are processed in decreasing order of their messages,
+// so the lanes of a warp run edge loops of equal length.  Weights come in the
+// composed layout (dss_layout.cuh) and the arithmetic runs on packed pairs of
+// FP32 lanes: a matrix-vector product issues one fma.rn.f32x2 per two outputs.
+// Out-messages to halo neighbours are masked (multiplied by 0) rather than
+// branched over.  Shared memory: per needed node its neighbour projections as
+// five float4 (Wb_out h pair m, Wb_in h pair m) and its scaled coordinates.
+template <int T>
+__device__ __forceinline__ void fused_project(const FusedWeights &W, const float (&h)[D], float4 *dst) {
+    const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
+    f2_t acc[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc[q] = 0ull;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const f2_t xi = f2_pack(h[i], h[i]);
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc[q] = f2_fma(Wp[(F_HB + i * 2 * D) / 2 + q], xi, acc[q]);
+    }
+#pragma unroll
+    for (int m = 0; m < D / 2; ++m) {
+        float a0, a1, b0, b1;
+        f2_unpack(acc[2 * m], a0, a1);
+        f2_unpack(acc[2 * m + 1], b0, b1);
+        dst[m] = make_float4(a0, a1, b0, b1);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid_constant__ FusedWeights W,
+                                                                  const __grid_constant__ ChunkArgs a) {
+    extern __shared__ __align__(16) float4 smem4[];
+    if (a.stop && *a.stop) return;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const int own = a.c_own[q];
+    const int nn = a.c_need_n[q];
+    const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
+    float4 *Pb = smem4;                                               // [nn][5]
+    float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
+    const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
+    // phase A: projections and coordinates of every needed node
+    for (int u = tid; u < nn; u += T) {
+        const int node = need[u];
+        float h[D];
+#pragma unroll
+        for (int o = 0; o < D; ++o) h[o] = a.first ? 0.f : a.h_in[o * a.n_total + node];
+        fused_project<T>(W, h, Pb + (size_t)u * 5);
+        XY[u] = a.loc_xy[node];
+    }
+    __syncthreads();
+    const int *aptr = a.adj_ptr + a.c_adj_off[q];
+    const uint16_t *adj = a.adj + a.c_adj_base[q];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int u = p * T + tid;
+        if (u >= own) continue;
+        const int node = need[u];
+        float hp[D];  // read again (a cache hit) rather than held across the barrier
+#pragma unroll
+        for (int o = 0; o < D; ++o) hp[o] = a.first ? 0.f : a.h_in[o * a.n_total + node];
+        const int g = a.gid[node];
+        const int j = node - a.loc_ptr[g];
+        const bool inner = j < a.loc_nint[g];
+        const int s0 = a.sub_ptr[g];
+        const double s = a.s[g];
+        float c;
+        if (a.first) {
+            c = (inner && s != 0.0) ? (float)(a.r[a.sub_idx[s0 + j]] / s) : 0.f;
+            a.c[node] = c;
+        } else {
+            c = a.c[node];
+        }
+        const float2 xj = XY[u];
+        f2_t pao[D / 2], pai[D / 2], so[D / 2], si[D / 2];
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) {
+            pao[m] = Wp[F_BA / 2 + m];
+            pai[m] = Wp[(F_BA + D) / 2 + m];
+            so[m] = 0ull;
+            si[m] = 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const f2_t xi = f2_pack(hp[i], hp[i]);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                pao[m] = f2_fma(Wp[(F_HA + i * 3 * D) / 2 + m], xi, pao[m]);
+                pai[m] = f2_fma(Wp[(F_HA + i * 3 * D + D) / 2 + m], xi, pai[m]);
+            }
+        }
+        const int e0 = aptr[u], e1 = aptr[u + 1];
+        float dout = 0.f;
+        for (int e = e0; e < e1; ++e) {
+            const unsigned ent = adj[e];
+            const int v = ent & 0x7fffu;
+            const float mo = (float)(ent >> 15);
+            dout += mo;
+            const float2 xl = XY[v];
+            const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+            const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
+            const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn), mo2 = f2_pack(mo, mo);
+            const float4 *pb = Pb + (size_t)v * 5;
+            float4 t[D / 2];
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) t[m] = pb[m];
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                f2_t z = f2_add(pao[m], f2_pack(t[m].x, t[m].y));
+                z = f2_fma(Wp[F_WEO / 2 + m], dx2, z);
+                z = f2_fma(Wp[(F_WEO + D) / 2 + m], dy2, z);
+                z = f2_fma(Wp[(F_WEO + 2 * D) / 2 + m], dn2, z);
+                so[m] = f2_fma(f2_relu(z), mo2, so[m]);
+            }
+            if (inner) {
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    f2_t z = f2_add(pai[m], f2_pack(t[m].z, t[m].w));
+                    z = f2_fma(Wp[F_WEI / 2 + m], dx2, z);
+                    z = f2_fma(Wp[(F_WEI + D) / 2 + m], dy2, z);
+                    z = f2_fma(Wp[(F_WEI + 2 * D) / 2 + m], dn2, z);
+                    si[m] = f2_add(si[m], f2_relu(z));
+                }
+            }
+        }
+        const float din = inner ? (float)(e1 - e0) : 0.f;
+        // Psi hidden layer on [h, c, phi_out, phi_in] with the second message layers composed in
+        f2_t hid[D / 2];
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) hid[m] = Wp[(F_BA + 2 * D) / 2 + m];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const f2_t xi = f2_pack(hp[i], hp[i]);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) hid[m] = f2_fma(Wp[(F_HA + i * 3 * D + 2 * D) / 2 + m], xi, hid[m]);
+        }
+        {
+            const f2_t cc = f2_pack(c, c), dd = f2_pack(dout, dout), di = f2_pack(din, din);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                hid[m] = f2_fma(Wp[F_VC / 2 + m], cc, hid[m]);
+                hid[m] = f2_fma(Wp[F_VO / 2 + m], dd, hid[m]);
+                hid[m] = f2_fma(Wp[F_VI / 2 + m], di, hid[m]);
+            }
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < D / 2; ++i2) {
+            float o0, o1, n0, n1;
+            f2_unpack(so[i2], o0, o1);
+            f2_unpack(si[i2], n0, n1);
+            const f2_t a0 = f2_pack(o0, o0), a1 = f2_pack(o1, o1), b0 = f2_pack(n0, n0), b1 = f2_pack(n1, n1);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                hid[m] = f2_fma(Wp[(F_MO + 2 * i2 * D) / 2 + m], a0, hid[m]);
+                hid[m] = f2_fma(Wp[(F_MO + (2 * i2 + 1) * D) / 2 + m], a1, hid[m]);
+                hid[m] = f2_fma(Wp[(F_MI + 2 * i2 * D) / 2 + m], b0, hid[m]);
+                hid[m] = f2_fma(Wp[(F_MI + (2 * i2 + 1) * D) / 2 + m], b1, hid[m]);
+            }
+        }
+        // h += alpha (Psi_W2 relu(hid) + Psi_b2)
+        f2_t out[D / 2];
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) out[m] = Wp[F_PB2 / 2 + m];
+#pragma unroll
+        for (int i2 = 0; i2 < D / 2; ++i2) {
+            float r0, r1;
+            f2_unpack(hid[i2], r0, r1);
+            const f2_t a0 = f2_pack(relu(r0), relu(r0)), a1 = f2_pack(relu(r1), relu(r1));
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                out[m] = f2_fma(Wp[(F_P2 + 2 * i2 * D) / 2 + m], a0, out[m]);
+                out[m] = f2_fma(Wp[(F_P2 + (2 * i2 + 1) * D) / 2 + m], a1, out[m]);
+            }
+        }
+        float hn[D];
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) {
+            const f2_t hv = f2_add(f2_pack(hp[2 * m], hp[2 * m + 1]), out[m]);
+            f2_unpack(hv, hn[2 * m], hn[2 * m + 1]);
+        }
+        if (a.last) {
+            if (inner) {
+                f2_t dh[D / 2];
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) dh[m] = Wp[F_DB1 / 2 + m];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const f2_t xi = f2_pack(hn[i], hn[i]);
+#pragma unroll
+                    for (int m = 0; m < D / 2; ++m) dh[m] = f2_fma(Wp[(F_DW1 + i * D) / 2 + m], xi, dh[m]);
+                }
+                float y = W.w[F_DB2];
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    float d0, d1;
+                    f2_unpack(dh[m], d0, d1);
+                    y = fmaf(W.w[F_DW2 + 2 * m], relu(d0), y);
+                    y = fmaf(W.w[F_DW2 + 2 * m + 1], relu(d1), y);
+                }
+                a.corr[s0 + j] = s == 0.0 ? 0.0 : s * (double)y;
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < D; ++o) a.h_out[o * a.n_total + node] = hn[o];
+        }
+    }
+}
+
+// Set-up of a global chunk plan, one CTA per chunk: the chunk's own nodes are the
+// local-node range [c_n0, c_n0 + c_own) of the concatenated graphs (a chunk may
+// span two graphs; edges never do).  Pass 0 counts needed nodes and adjacency
+// entries; pass 1 lists the own nodes in decreasing order of their messages per
+// block, then the outside neighbours (ascending), and writes the chunk-local
+// adjacency with bit 15 set for neighbours that are unknowns.
+__global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int *c_own, const int *gid,
+                                                      const int *loc_ptr, const int *loc_nint, const int *nbr_ptr,
+                                                      const int *nbr_off, const uint16_t *nbr, int pass, int *need_n,
+                                                      int *adj_n, const int *need_off, int *need, const int *adj_off,
+                                                      int *adj_ptr, const int *adj_base, uint16_t *adj, int *st) {
+    constexpr int NT = 256, MAXN = 2048, MAXO = 512;
+    __shared__ int cand[MAXN];
+    __shared__ int work[MAXO], slot[MAXO], order[MAXO], sptr[MAXO + 1];
+    __shared__ int cnt, uniq;
+    const int q = blockIdx.x;
+    const int o0 = c_n0[q], own = c_own[q];
+    if (own > MAXO) {
+        if (threadIdx.x == 0) raise_status(st, ST_TOO_LARGE);
+        return;
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    // neighbours of own node t: local ids of its graph, as global local-node ids
+    auto row = [&](int t, int &g, int &lp, int &e0, int &e1) {
+        const int u = o0 + t;
+        g = gid[u];
+        lp = loc_ptr[g];
+        const int *gptr = nbr_ptr + lp + g;
+        e0 = gptr[u - lp];
+        e1 = gptr[u - lp + 1];
+    };
+    for (int t = threadIdx.x; t < own; t += NT) {
+        int g, lp, e0, e1;
+        row(t, g, lp, e0, e1);
+        const uint16_t *gn = nbr + nbr_off[g];
+        for (int e = e0; e < e1; ++e) {
+            const int l = lp + gn[e];
+            if (l < o0 || l >= o0 + own) {
+                const int pos = atomicAdd(&cnt, 1);
+                if (pos < MAXN) cand[pos] = l;
+            }
+        }
+    }
+    __syncthreads();
+    const int m = cnt;
+    if (m > MAXN) {
+        if (threadIdx.x == 0) raise_status(st, ST_TOO_LARGE);
+        return;
+    }
+    int N = 1;
+    while (N < m) N <<= 1;
+    for (int t = m + threadIdx.x; t < N; t += NT) cand[t] = INT_MAX;
+    __syncthreads();
+    for (int kk = 2; kk <= N; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < N; t += NT) {
+                const int r = t ^ jj;
+                if (r > t) {
+                    const bool up = (t & kk) == 0;
+                    const int x = cand[t], y = cand[r];
+                    if ((x > y) == up) {
+                        cand[t] = y;
+                        cand[r] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        int u = 0;
+        for (int t = 0; t < m; ++t)
+            if (t == 0 || cand[t] != cand[t - 1]) cand[u++] = cand[t];
+        uniq = u;
+    }
+    __syncthreads();
+    const int ext = uniq;
+    if (pass == 0) {
+        if (threadIdx.x == 0) {
+            need_n[q] = own + ext;
+            int tot = 0;
+            for (int t = 0; t < own; ++t) {
+                int g, lp, e0, e1;
+                row(t, g, lp, e0, e1);
+                tot += e1 - e0;
+            }
+            adj_n[q] = tot;
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < own; t += NT) {
+        int g, lp, e0, e1;
+        row(t, g, lp, e0, e1);
+        const uint16_t *gn = nbr + nbr_off[g];
+        const int k = loc_nint[g];
+        int w = 0;
+        for (int e = e0; e < e1; ++e) w += gn[e] < k ? 1 : 0;
+        if (o0 + t - lp < k) w += e1 - e0;
+        work[t] = w;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < own; t += NT) {  // rank: more messages first, then lower id
+        int r = 0;
+        for (int u = 0; u < own; ++u) r += (work[u] > work[t] || (work[u] == work[t] && u < t)) ? 1 : 0;
+        slot[t] = r;
+        order[r] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sptr[0] = 0;
+        for (int r = 0; r < own; ++r) {
+            int g, lp, e0, e1;
+            row(order[r], g, lp, e0, e1);
+            sptr[r + 1] = sptr[r] + e1 - e0;
+        }
+    }
+    __syncthreads();
+    int *nd = need + need_off[q];
+    int *ap = adj_ptr + adj_off[q];
+    uint16_t *ad = adj + adj_base[q];
+    for (int r = threadIdx.x; r < own; r += NT) nd[r] = o0 + order[r];
+    for (int t = threadIdx.x; t < ext; t += NT) nd[own + t] = cand[t];
+    for (int r = threadIdx.x; r <= own; r += NT) ap[r] = sptr[r];
+    for (int r = threadIdx.x; r < own; r += NT) {
+        int g, lp, e0, e1;
+        row(order[r], g, lp, e0, e1);
+        const uint16_t *gn = nbr + nbr_off[g];
+        const int k = loc_nint[g];
+        int pos = sptr[r];
+        for (int e = e0; e < e1; ++e, ++pos) {
+            const int l = lp + gn[e];
+            int v;
+            if (l >= o0 && l < o0 + own) {
+                v = slot[l - o0];
+            } else {
+                int lo = 0, hi = ext;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cand[mid] < l) lo = mid + 1; else hi = mid;
+                }
+                v = own + lo;
+            }
+            ad[pos] = (uint16_t)(v | (gn[e] < k ? 0x8000 : 0));
+        }
+    }
+}
+
 // set-up of the chunks of one graph per CTA: needed-node lists and chunk-local adjacency.
 // Pass 0 counts (needed nodes, adjacency entries) per chunk; pass 1 fills.
 constexpr int CH_T = 256;
@@ -779,6 +1243,8 @@ void chunk_free(ddg_problem *p) {
     p->chunk.c_graph = p->chunk.c_n0 = p->chunk.c_own = p->chunk.c_need_off = p->chunk.c_need_n = nullptr;
     p->chunk.need = p->chunk.c_adj_off = p->chunk.adj_ptr = p->chunk.c_adj_base = nullptr;
     p->chunk.adj = nullptr;
+    p->chunk.gid = nullptr;
+    p->chunk.global = false;
     (void)empty;
 }
 
@@ -869,8 +1335,131 @@ static int32_t launch_chunks(ddg_problem *p, const ChunkArgs &base, cudaStream_t
         a.last = blk == m->kbar - 1;
         a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
         a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
-        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(m->packed_host.data()) + blk;
+        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(w_packed_host(p)) + blk;
         k_dss_chunk<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
+    }
+    DDG_LAUNCHES(m->kbar);
+    return DDG_OK;
+}
+
+template <int T>
+static int32_t fused_configure() {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        configured = true;
+    }
+    return DDG_OK;
+}
+
+template <int T>
+static int32_t fused_ctas_per_sm(size_t smem, int *out) {
+    DDG_TRY(fused_configure<T>());
+    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dss_fused<T>, T, smem));
+    return DDG_OK;
+}
+
+// Global chunk plan of schedule 3: the concatenated graphs' nodes cut into
+// equal ranges, as many as fill every SM's resident CTAs a whole number of
+// times (at most 2T nodes each), so every SM gets the same work per block.
+int32_t chunk_build_global(ddg_problem *p, int T) {
+    ddg_ctx *c = p->ctx;
+    cudaStream_t s = p->stream;
+    chunk_free(p);
+    ChunkPlan &cp = p->chunk;
+    const long long n = p->sum_loc;
+    const int K = p->K;
+    int sms = 0, per_sm = 0;
+    DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const size_t smem_est = (size_t)3 * T * (5 * sizeof(float4) + sizeof(float2));  // 2T own + T outside
+    switch (T) {
+        case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
+        case 192: DDG_TRY(fused_ctas_per_sm<192>(smem_est, &per_sm)); break;
+        case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
+        default: set_error("chunk width must be 128, 192 or 256"); return DDG_INVALID_ARG;
+    }
+    const long long slots = (long long)sms * std::max(1, per_sm);
+    const long long waves = std::max(1LL, (n + slots * 2 * T - 1) / (slots * 2 * T));
+    const long long cs = (n + slots * waves - 1) / (slots * waves);
+    const int nc = (int)((n + cs - 1) / cs);
+    std::vector<int> lp(K + 1), gid(n), cn0(nc), cown(nc);
+    DDG_CU(cudaMemcpyAsync(lp.data(), p->loc_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    for (int g = 0; g < K; ++g)
+        for (int u = lp[g]; u < lp[g + 1]; ++u) gid[u] = g;
+    for (int q = 0; q < nc; ++q) {
+        cn0[q] = (int)(q * cs);
+        cown[q] = (int)std::min(cs, n - q * cs);
+    }
+    cp.T = T;
+    cp.global = true;
+    cp.nchunks = nc;
+    DDG_TRY(dalloc(c, cp.allocs, &cp.gid, n));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_n0, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_own, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_off, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_n, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_off, nc));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_base, nc));
+    DDG_CU(cudaMemcpyAsync(cp.gid, gid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    int *adj_n = nullptr;
+    DDG_CU(cudaMallocAsync(&adj_n, sizeof(int) * nc, s));
+    k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
+                                      p->nbr, 0, cp.c_need_n, adj_n, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, p->d_status);
+    DDG_LAUNCH_CHECK();
+    std::vector<int> hn(nc), ha(nc);
+    DDG_CU(cudaMemcpyAsync(hn.data(), cp.c_need_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaMemcpyAsync(ha.data(), adj_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    DDG_TRY(check_status(p, "GNN chunks"));
+    std::vector<int> noff(nc), aoff(nc), abase(nc);
+    long long tn = 0, ta = 0, tp = 0;
+    int maxn = 0;
+    for (int q = 0; q < nc; ++q) {
+        noff[q] = (int)tn;
+        abase[q] = (int)ta;
+        aoff[q] = (int)tp;
+        tn += hn[q];
+        ta += ha[q];
+        tp += cown[q] + 1;
+        maxn = std::max(maxn, hn[q]);
+    }
+    cp.max_need = maxn;
+    DDG_TRY(dalloc(c, cp.allocs, &cp.need, tn));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.adj, ta));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.adj_ptr, tp));
+    DDG_CU(cudaMemcpyAsync(cp.c_need_off, noff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_adj_off, aoff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    DDG_CU(cudaMemcpyAsync(cp.c_adj_base, abase.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
+                                      p->nbr, 1, nullptr, nullptr, cp.c_need_off, cp.need, cp.c_adj_off, cp.adj_ptr,
+                                      cp.c_adj_base, cp.adj, p->d_status);
+    DDG_LAUNCH_CHECK();
+    DDG_CU(cudaFreeAsync(adj_n, s));
+    DDG_CU(cudaStreamSynchronize(s));
+    return check_status(p, "GNN chunks");
+}
+
+template <int T>
+static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t s) {
+    DDG_TRY(fused_configure<T>());
+    const ddg_model *m = p->model;
+    const size_t smem = (size_t)p->chunk.max_need * (5 * sizeof(float4) + sizeof(float2));
+    if (smem > 227 * 1024) {
+        set_error("a GNN chunk needs more shared memory than a CTA has");
+        return DDG_TOO_LARGE;
+    }
+    for (int blk = 0; blk < m->kbar; ++blk) {
+        ChunkArgs a = base;
+        a.first = blk == 0;
+        a.last = blk == m->kbar - 1;
+        a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
+        a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
+        const FusedWeights *W = reinterpret_cast<const FusedWeights *>(w_fused_host(p)) + blk;
+        k_dss_fused<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
     }
     DDG_LAUNCHES(m->kbar);
     return DDG_OK;
@@ -891,6 +1480,7 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.c_adj_base = cp.c_adj_base;
     a.loc_ptr = p->loc_ptr;
     a.loc_nint = p->loc_nint;
+    a.gid = cp.gid;
     a.sub_ptr = p->sub_ptr;
     a.sub_idx = p->sub_idx;
     a.loc_xy = p->loc_xy;
@@ -901,6 +1491,14 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.n_total = p->sum_loc;
     a.alpha = p->model->alpha;
     a.stop = stop;
+    if (cp.global) {
+        switch (cp.T) {
+            case 128: return launch_fused<128>(p, a, s);
+            case 192: return launch_fused<192>(p, a, s);
+            case 256: return launch_fused<256>(p, a, s);
+            default: set_error("no chunk plan"); return DDG_INVALID_ARG;
+        }
+    }
     switch (cp.T) {
         case 128: return launch_chunks<128>(p, a, s);
         case 192: return launch_chunks<192>(p, a, s);
@@ -942,7 +1540,7 @@ static int32_t launch_steps(ddg_problem *p, const DssStepArgs &base, size_t smem
         DssStepArgs a = base;
         a.first = blk == 0;
         a.last = blk == m->kbar - 1;
-        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(m->packed_host.data()) + blk;
+        const BlockWeights *W = reinterpret_cast<const BlockWeights *>(w_packed_host(p)) + blk;
         k_dss_step<P><<<p->K, DSS_THREADS, smem, s>>>(*W, a);
     }
     DDG_LAUNCHES(m->kbar);
@@ -981,10 +1579,10 @@ int32_t dss_step_launch(ddg_problem *p, const double *r, const int *stop, cudaSt
 
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     if (p->dss_sched == 1) return dss_step_launch(p, r, stop, s);
-    if (p->dss_sched == 2) return dss_chunk_launch(p, r, stop, s);
+    if (p->dss_sched == 2 || p->dss_sched == 3) return dss_chunk_launch(p, r, stop, s);
     const ddg_model *m = p->model;
     DssArgs a;
-    a.weights = m->packed;
+    a.weights = w_packed_dev(p);
     a.kbar = m->kbar;
     a.alpha = m->alpha;
     a.order = p->lpt_order;
@@ -1014,16 +1612,16 @@ int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaSt
     }
 }
 
+// Schedules 0 and 1 hold a whole local graph in one CTA's shared memory (at most
+// DSS_MAX_NODES nodes); the chunked schedules 2 and 3 take graphs up to the
+// 16-bit local ids' limit, e.g. the paper's sub-meshes of 2,000 nodes with overlap.
 int32_t dss_check_capacity(ddg_problem *p) {
-    if (p->max_loc > DSS_MAX_NODES) {
-        set_error("local graph of " + std::to_string(p->max_loc) + " nodes exceeds the GNN kernel's " +
-                  std::to_string(DSS_MAX_NODES));
+    if (p->max_loc > 65535) {
+        set_error("local graph of " + std::to_string(p->max_loc) + " nodes exceeds the 65,535 nodes of 16-bit local ids");
         return DDG_TOO_LARGE;
     }
-    if (p->max_edges > 65535 || dss_smem_bytes(p->max_loc, p->max_edges) > 227 * 1024) {
-        set_error("local graph does not fit the GNN kernel's shared memory");
-        return DDG_TOO_LARGE;
-    }
+    p->dss_whole_graph = p->max_loc <= DSS_MAX_NODES && p->max_edges <= 65535 &&
+                         dss_smem_bytes(p->max_loc, p->max_edges) <= 227 * 1024;
     return DDG_OK;
 }
 

@@ -35,6 +35,65 @@ constexpr int BLOCK_FLOATS = OFF_DEC + DEC_SIZE;  // 1504
 constexpr int BLOCK_BYTES = BLOCK_FLOATS * 4;     // 6016, a multiple of 16
 static_assert(BLOCK_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 
+// ---------------------------------------------------------------- fused layout (schedule 3)
+// Per block, every matrix stored input-major ([in][out]) so that consecutive
+// outputs form 8-byte pairs for the packed two-lane FP32 instructions:
+//   HB  [D][2D]  Wb_out and Wb_in interleaved by output pairs (o0 o1 i0 i1 o2 o3 ...),
+//                the layout of a node's neighbour projections in shared memory
+//   HA  [D][3D]  Wa_out | Wa_in | the h-columns of Psi's first layer;  BA [3D] their biases
+//   WEO [3][D]   We_out for (dx, dy, |d|);  WEI [3][D] We_in for (-dx, -dy, |d|), signs folded in
+//   MO, MI [D][D]  Psi_W1(phi_out cols) W2_out and Psi_W1(phi_in cols) W2_in, composed
+//   VC [D]       Psi_W1 column of c;  VO, VI [D]  Psi_W1(phi cols) b2 (times the degree)
+//   P2 [D][D]    alpha Psi_W2;  PB2 [D]  alpha Psi_b2
+//   DW1 [D][D], DB1 [D], DW2 [D], DB2 [2]  decoder
+// The compositions are exact in real arithmetic:
+//   Psi_W1 [.., phi, ..] with phi = W2 S + deg b2  =  (Psi_W1 W2) S + deg (Psi_W1 b2).
+constexpr int F_HB = 0;
+constexpr int F_HA = F_HB + D * 2 * D;
+constexpr int F_BA = F_HA + D * 3 * D;
+constexpr int F_WEO = F_BA + 3 * D;
+constexpr int F_WEI = F_WEO + 3 * D;
+constexpr int F_MO = F_WEI + 3 * D;
+constexpr int F_MI = F_MO + D * D;
+constexpr int F_VC = F_MI + D * D;
+constexpr int F_VO = F_VC + D;
+constexpr int F_VI = F_VO + D;
+constexpr int F_P2 = F_VI + D;
+constexpr int F_PB2 = F_P2 + D * D;
+constexpr int F_DW1 = F_PB2 + D;
+constexpr int F_DB1 = F_DW1 + D * D;
+constexpr int F_DW2 = F_DB1 + D;
+constexpr int F_DB2 = F_DW2 + D;
+constexpr int F_FLOATS = F_DB2 + 2;  // 1052
+static_assert(F_FLOATS % 2 == 0 && F_HA % 2 == 0 && F_MO % 2 == 0 && F_P2 % 2 == 0 && F_DW1 % 2 == 0,
+              "every pair starts on an 8-byte boundary");
+
+struct alignas(16) FusedWeights {
+    float w[F_FLOATS];
+};
+
+// ---------------------------------------------------------------- packed two-lane FP32 (f32x2)
+typedef unsigned long long f2_t;  // lanes (lo, hi)
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ReLU as max(x, 0) that keeps a NaN input (max.NaN); fmaxf would return 0 for it
 __device__ __forceinline__ float relu(float x) {
     float r;
@@ -111,6 +170,19 @@ __device__ __forceinline__ void edge_msg(float (&S)[D], const float (&Pa)[D], co
         z = fmaf(We[2 * DP + o], en, z);
         S[o] += relu(z);
     }
+}
+
+__device__ __forceinline__ f2_t f2_relu(f2_t v) {
+    float lo, hi;
+    f2_unpack(v, lo, hi);
+    return f2_pack(relu(lo), relu(hi));
+}
+
+// square root by the hardware approximation (relative error near one ulp)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 }  // namespace ddg

@@ -192,16 +192,22 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 // Picks the fastest GNN schedule for this decomposition by timing each on the
 // right-hand side: 0 = one persistent launch per application; 1 = one launch
 // per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
-// the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256).
-// DDG_GNN_SCHEDULE = 0, 1, 2 (and DDG_GNN_CHUNK_T = 128/192/256) forces one.
+// the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256); 3 = the
+// chunks of 2 with composed weights, packed two-lane FP32 and message-sorted nodes.
+// DDG_GNN_SCHEDULE = 0..3 (and DDG_GNN_CHUNK_T = 128/192/256) forces one.
 // The choice is cached in the context per decomposition shape class, so a stream
 // of requests of similar sizes tunes once.
 int32_t dss_autotune(ddg_problem *p) {
     const char *env = getenv("DDG_GNN_SCHEDULE");
     const char *envT = getenv("DDG_GNN_CHUNK_T");
-    if (env && (env[0] == '0' || env[0] == '1' || env[0] == '2')) {
+    if (env && env[0] >= '0' && env[0] <= '3' && env[1] == 0) {
         p->dss_sched = env[0] - '0';
+        if (p->dss_sched < 2 && !p->dss_whole_graph) {
+            set_error("GNN schedules 0 and 1 need every local graph in one CTA; use 2 or 3");
+            return DDG_TOO_LARGE;
+        }
         if (p->dss_sched == 2) DDG_TRY(chunk_build(p, envT ? atoi(envT) : 192));
+        if (p->dss_sched == 3) DDG_TRY(chunk_build_global(p, envT ? atoi(envT) : 256));
         return DDG_OK;
     }
     const long long cls_K = (long long)std::floor(4.0 * std::log2((double)p->K));
@@ -212,7 +218,7 @@ int32_t dss_autotune(ddg_problem *p) {
         {
             std::lock_guard<std::mutex> lock(p->ctx->tune_mu);
             for (const auto &t : p->ctx->tuned)
-                if (t.K == cls_K && t.nodes == cls_n && t.max_loc == cls_m) {
+                if (t.K == cls_K && t.nodes == cls_n && t.max_loc == cls_m && (t.sched >= 2 || p->dss_whole_graph)) {
                     cached = t.sched;
                     cachedT = t.T;
                 }
@@ -220,6 +226,7 @@ int32_t dss_autotune(ddg_problem *p) {
         if (cached >= 0) {
             p->dss_sched = cached;
             if (cached == 2) DDG_TRY(chunk_build(p, cachedT));
+            if (cached == 3) DDG_TRY(chunk_build_global(p, cachedT));
             return DDG_OK;
         }
     }
@@ -229,10 +236,12 @@ int32_t dss_autotune(ddg_problem *p) {
     DDG_CU(cudaEventCreate(&e1));
     float best = 1e30f;
     int pick = 0, pickT = 0;
-    const int cands[5][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}};
+    const int cands[8][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}, {3, 128}, {3, 192}, {3, 256}};
     for (const auto &cd : cands) {
+        if (cd[0] < 2 && !p->dss_whole_graph) continue;
         p->dss_sched = cd[0];
         if (cd[0] == 2) DDG_TRY(chunk_build(p, cd[1]));
+        if (cd[0] == 3) DDG_TRY(chunk_build_global(p, cd[1]));
         DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
         DDG_CU(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 2; ++rep) DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
@@ -249,8 +258,9 @@ int32_t dss_autotune(ddg_problem *p) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->dss_sched = pick;
-    if (pick == 2) {
-        if (p->chunk.T != pickT) DDG_TRY(chunk_build(p, pickT));
+    if (pick >= 2) {
+        if (p->chunk.T != pickT || p->chunk.global != (pick == 3))
+            DDG_TRY(pick == 3 ? chunk_build_global(p, pickT) : chunk_build(p, pickT));
     } else {
         chunk_free(p);
     }
@@ -689,7 +699,7 @@ struct FcgRun {
         rp.launches = launches;
         rp.local_applies = loc_applies;
         rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
-        rp.gnn_chunk_t = (p->kind == DDG_DDM_GNN && p->dss_sched == 2) ? p->chunk.T : 0;
+        rp.gnn_chunk_t = (p->kind == DDG_DDM_GNN && p->dss_sched >= 2) ? p->chunk.T : 0;
         rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
         if (rep) *rep = rp;
         release();

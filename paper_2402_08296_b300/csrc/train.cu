@@ -816,8 +816,7 @@ int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o,
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    m->packed_host.resize((size_t)m->kbar * BLOCK_FLOATS);
-    DDG_CU(cudaMemcpy(m->packed_host.data(), m->packed, sizeof(float) * m->packed_host.size(), cudaMemcpyDeviceToHost));
+    DDG_TRY(model_host_layouts(m));
     if (rep) {
         rep->samples = n_samples;
         rep->steps = o->steps;

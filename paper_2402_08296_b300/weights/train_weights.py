@@ -9,8 +9,8 @@ Adam state lives in the model, so the meshes form one optimisation; the
 learning rate drops x0.1 when the mean loss of a round over all meshes stops
 improving.
 
-Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15
-Writes dss_k30_d10.npy (flat float32 weights, layout of include/ddg.h).
+Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15 [--kbar 30]
+Writes dss_k{kbar}_d10.npy (flat float32 weights, layout of include/ddg.h).
 """
 from __future__ import annotations
 
@@ -27,7 +27,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import paper_2402_08296_b300 as ddg  # noqa: E402
 import synth  # noqa: E402
 
-KBAR, D, ALPHA = 30, 10, 1e-3
+D, ALPHA = 10, 1e-3
 
 
 def main():
@@ -38,9 +38,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200, help="optimiser steps per mesh and round")
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--harvest", type=int, default=60)
-    ap.add_argument("--out", default=os.path.join(HERE, "dss_k30_d10.npy"))
+    ap.add_argument("--kbar", type=int, default=30, help="message-passing blocks (Section III-B)")
+    ap.add_argument("--out", default=None)
     ap.add_argument("--log", default=None)
     a = ap.parse_args()
+    KBAR = a.kbar
+    if a.out is None:
+        a.out = os.path.join(HERE, f"dss_k{KBAR}_d{D}.npy")
     log = open(a.log, "w") if a.log else sys.stdout
     ctx = ddg.ddg_create(0)
     model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, None, seed=2024)

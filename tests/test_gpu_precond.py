@@ -112,6 +112,143 @@ def test_dss_local_corrections(ddg, ctx, torch, name, seed, K, delta, alpha, bia
         ddg.ddg_model_destroy(m)
 
 
+@pytest.mark.parametrize("schedule,chunk_t", [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256")])
+def test_dss_local_corrections_every_schedule(ddg, ctx, torch, schedule, chunk_t, monkeypatch):
+    """Every GNN schedule against the FP64 oracle on ragged ~1,300-node graphs; with
+    T = 128 each graph spans several chunks, so chunk borders and halos are exercised."""
+    monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
+    if chunk_t:
+        monkeypatch.setenv("DDG_GNN_CHUNK_T", chunk_t)
+    name, seed, K, delta, alpha, bias = "star20000", 4, 20, 2, 0.02, 0.1
+    w = synth.workload(name, seed)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    W = _weights(seed, bias)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    m = ddg.ddg_model_create(ctx, KBAR, D, alpha, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        r = synth.residual_vector(P.n_free, seed + 30)
+        rd = _dev(torch, r)
+        sk = sum(len(S) for S in Dd.sets)
+        corr = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        s = torch.zeros(K, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr = corr.cpu().numpy()
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        off = 0
+        for i, S in enumerate(Dd.sets):
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, D, alpha, hbar)
+            got = corr[off:off + len(S)]
+            off += len(S)
+            assert rel(got, ref) < 1e-4, (schedule, i, rel(got, ref))
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+@pytest.mark.parametrize("schedule", ["2", "3"])
+def test_dss_sub_meshes_of_2000_nodes(ddg, ctx, torch, schedule, monkeypatch):
+    """Sub-meshes of ~2,000 unknowns (Section V-B's largest N_s) give local graphs beyond one
+    CTA; the chunked schedules run them and match the oracle, the whole-graph ones refuse."""
+    name, seed, delta, alpha, bias = "star20000", 6, 2, 0.02, 0.1
+    w = synth.workload(name, seed)
+    P, _ = oracle_setup(w.mesh, w.coeffs, 1, delta)
+    K = max(1, int(round(P.n_free / 2000)))
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    assert max(len(S) for S in Dd.sets) > 2048
+    W = _weights(seed, bias)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    m = ddg.ddg_model_create(ctx, KBAR, D, alpha, W)
+    try:
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", "1")
+        with pytest.raises(ddg.DdgError):
+            ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
+        monkeypatch.setenv("DDG_GNN_CHUNK_T", "256")
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        r = synth.residual_vector(P.n_free, seed + 30)
+        rd = _dev(torch, r)
+        sk = sum(len(S) for S in Dd.sets)
+        corr = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        s = torch.zeros(K, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr = corr.cpu().numpy()
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        off = 0
+        for i, S in enumerate(Dd.sets):
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, D, alpha, hbar)
+            got = corr[off:off + len(S)]
+            off += len(S)
+            assert rel(got, ref) < 1e-4, (schedule, i, rel(got, ref))
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+def _round_bf16(w):
+    """float32 -> nearest bfloat16 value (ties to even), kept as float32."""
+    b = np.asarray(w, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return b.view(np.float32)
+
+
+def test_dss_bf16_weights(ddg, ctx, torch):
+    """DDG_BF16_WEIGHTS: the GNN with its weights rounded to bfloat16 equals the FP64 oracle run
+    on the rounded weights (1e-4) and stays within 2e-2 of the unrounded model."""
+    name, seed, K, delta, alpha, bias = "star20000", 7, 20, 2, 1e-3, 0.05
+    w = synth.workload(name, seed)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    W = _weights(seed, bias)
+    Wb = _round_bf16(W)
+    assert np.all(Wb.view(np.uint32) & 0xFFFF == 0) and not np.array_equal(W, Wb)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    m = ddg.ddg_model_create(ctx, KBAR, D, alpha, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE | ddg.DDG_BF16_WEIGHTS)
+        r = synth.residual_vector(P.n_free, seed + 30)
+        rd = _dev(torch, r)
+        sk = sum(len(S) for S in Dd.sets)
+        corr = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        s = torch.zeros(K, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr = corr.cpu().numpy()
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        off = 0
+        for i, S in enumerate(Dd.sets[:8]):
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            c = r[S] / si
+            ref_b = si * dss.forward(g.xy, g.n_int, g.src, g.dst, c, Wb, KBAR, D, alpha, hbar)
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, c, W, KBAR, D, alpha, hbar)
+            got = corr[off:off + len(S)]
+            off += len(S)
+            assert rel(got, ref_b) < 1e-4, (i, rel(got, ref_b))
+            assert rel(got, ref) < 2e-2, (i, rel(got, ref))
+        # the flag is per set-up: without it the model's own weights are used again
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        corr2 = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr2, s)
+        torch.cuda.synchronize()
+        S = Dd.sets[0]
+        g = pt.local_graph(P, S, adj)
+        si = np.linalg.norm(r[S])
+        ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, D, alpha, hbar)
+        assert rel(corr2.cpu().numpy()[:len(S)], ref) < 1e-4
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
 @pytest.mark.parametrize("pou", [False, True])
 def test_ddm_gnn_precondition(ddg, ctx, torch, pou):
     w = synth.workload("square2k", 4)

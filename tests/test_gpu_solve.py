@@ -131,7 +131,7 @@ def test_failures_are_status_codes(ddg, ctx):
         ddg.ddg_problem_destroy(p)
 
 
-@pytest.mark.parametrize("schedule", ["0", "1", "2"])
+@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
 def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, schedule, monkeypatch):
     """Both GNN schedules give the same local corrections; the CUDA-graph replay of the FCG
     period gives the same iterates as direct launches."""

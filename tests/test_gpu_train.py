@@ -91,3 +91,41 @@ def test_training_reduces_the_loss():
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)
         ddg.ddg_destroy(ctx)
+
+
+def test_autograd_function_trains_through_the_hand_written_backward():
+    """dss_residual_loss: torch.autograd sees the library's loss and gradient; a few Adam
+    steps of torch.optim through it lower the loss, and ddg_model_set_weights round-trips."""
+    import torch
+    import paper_2402_08296_b300 as ddg
+    kbar, alpha = 4, 0.1
+    w = synth.workload("square2k", 5)
+    P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
+    W0 = synth.dss_weights(kbar, D, 11, bias_scale=0.05)
+    r = synth.residual_vector(P.n_free, 12)
+    ctx = ddg.ddg_create(0)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    m = ddg.ddg_model_create(ctx, kbar, D, alpha, W0)
+    try:
+        rd = torch.as_tensor(r).cuda()
+        graphs = [0, 1, 2, 3]
+        wt = torch.nn.Parameter(torch.as_tensor(W0).cuda())
+        loss = ddg.dss_residual_loss(wt, p, m, rd, graphs)
+        loss.backward()
+        l_ref, g_ref = ddg.ddg_train_loss_grad(p, m, rd, graphs, W0.size)
+        assert float(loss) == l_ref
+        assert np.array_equal(wt.grad.cpu().numpy(), g_ref)
+        assert np.array_equal(ddg.ddg_model_get_weights(m, W0.size), W0)
+        opt = torch.optim.Adam([wt], lr=1e-3)
+        first = float(loss)
+        for _ in range(30):
+            opt.zero_grad()
+            loss = ddg.dss_residual_loss(wt, p, m, rd, graphs)
+            loss.backward()
+            opt.step()
+        assert float(loss) < first
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+        ddg.ddg_destroy(ctx)
+
