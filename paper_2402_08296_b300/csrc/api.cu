@@ -338,8 +338,9 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
     } else {
         DDG_TRY(dss_check_capacity(p));
         DDG_TRY(dss_select_weights(p, (flags & DDG_BF16_WEIGHTS) != 0));
-        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_D * p->sum_loc));
-        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, (size_t)DSS_D * p->sum_loc));
+        // latents: d planes of sum_loc (schedules 0-2) or rows of 12 floats, h then c (schedule 3)
+        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_HROW * p->sum_loc));
+        DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, (size_t)DSS_HROW * p->sum_loc));
         DDG_TRY(dalloc(c, p->a_pre, &p->dss_c, p->sum_loc));
         p->kind = kind;
         DDG_TRY(dss_autotune(p));

@@ -53,6 +53,7 @@ constexpr int MAX_NODE_NBR = 32;   // mesh neighbours of one node
 constexpr int MAX_MEMBERSHIP = 32; // subdomains holding one node
 constexpr int DSS_D = 10;          // latent size compiled into the GNN kernel
 constexpr int DSS_THREADS = 512;
+constexpr int DSS_HROW = 12;        // floats per latent row of the fused schedule (h[10], c, pad)
 constexpr int DSS_MAX_NODES = 2048; // local graph nodes (unknowns + halo) per CTA
 
 struct Server;  // request scheduler (serve.cu)
@@ -107,6 +108,7 @@ struct ChunkPlan {
     bool global = false;  // schedule 3: chunks are ranges of the concatenated graphs' nodes, sized to fill
                           // the GPU evenly; own nodes sorted by message count, neighbour kind in bit 15
     int *gid = nullptr;   // global: graph of every local node (sum_loc)
+    int4 *info = nullptr; // global: per own slot {node, corr index or -1, free index of r or -1, graph}
     int *c_graph = nullptr, *c_n0 = nullptr, *c_own = nullptr, *c_need_off = nullptr, *c_need_n = nullptr;
     int *need = nullptr, *c_adj_off = nullptr, *adj_ptr = nullptr, *c_adj_base = nullptr;
     uint16_t *adj = nullptr;
@@ -233,7 +235,7 @@ int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaSt
 int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
 int32_t chunk_build(ddg_problem *p, int T);
-int32_t chunk_build_global(ddg_problem *p, int T);
+int32_t chunk_build_global(ddg_problem *p, int variant);  // variant: chunk width (+1000: split edge loop)
 void chunk_free(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);

@@ -640,6 +640,7 @@ struct ChunkArgs {
     const int *c_adj_base;                  // per chunk: start of its slice in adj
     const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
     const int *gid;                         // global plans: graph of every local node
+    const int4 *info;                       // global plans: per own slot {node, corr idx, r idx, graph}
     const float2 *loc_xy;
     const double *r, *s;
     double *corr;
@@ -814,9 +815,45 @@ __device__ __forceinline__ void fused_project(const FusedWeights &W, const float
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid_constant__ FusedWeights W,
-                                                                  const __grid_constant__ ChunkArgs a) {
+// h (10 floats) and c of a local node from its 12-float latent row
+__device__ __forceinline__ void load_hrow(const float4 *rows, int node, float (&h)[D], float &c) {
+    const float4 r0 = rows[3 * (size_t)node], r1 = rows[3 * (size_t)node + 1], r2 = rows[3 * (size_t)node + 2];
+    h[0] = r0.x; h[1] = r0.y; h[2] = r0.z; h[3] = r0.w;
+    h[4] = r1.x; h[5] = r1.y; h[6] = r1.z; h[7] = r1.w;
+    h[8] = r2.x; h[9] = r2.y;
+    c = r2.z;
+}
+
+// acc[m] += sum_i W[OFF + i*STRIDE + 2m .. 2m+1] x_i  over i < D (pairs of outputs)
+template <int OFF, int STRIDE>
+__device__ __forceinline__ void f2_mv(f2_t (&acc)[D / 2], const f2_t *Wp, const float (&x)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const f2_t xi = f2_pack(x[i], x[i]);
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) acc[m] = f2_fma(Wp[(OFF + i * STRIDE) / 2 + m], xi, acc[m]);
+    }
+}
+
+// one message pair-block: acc += mask * relu(pa + pb + We e) over the five output pairs
+template <int OFF_WE, bool MASKED>
+__device__ __forceinline__ void f2_msg(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 2], const f2_t (&pb)[D / 2],
+                                       const f2_t *Wp, f2_t dx2, f2_t dy2, f2_t dn2, f2_t mask2) {
+#pragma unroll
+    for (int m = 0; m < D / 2; ++m) {
+        f2_t z = f2_add(pa[m], pb[m]);
+        z = f2_fma(Wp[OFF_WE / 2 + m], dx2, z);
+        z = f2_fma(Wp[(OFF_WE + D) / 2 + m], dy2, z);
+        z = f2_fma(Wp[(OFF_WE + 2 * D) / 2 + m], dn2, z);
+        acc[m] = MASKED ? f2_fma(f2_relu(z), mask2, acc[m]) : f2_add(acc[m], f2_relu(z));
+    }
+}
+
+// SPLIT runs the out- and in-messages in two passes over the neighbours (recomputing the
+// edge geometry) so that fewer accumulators are live at once: fewer registers, more warps.
+template <int T, bool SPLIT>
+__global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
+    k_dss_fused(const __grid_constant__ FusedWeights W, const __grid_constant__ ChunkArgs a) {
     extern __shared__ __align__(16) float4 smem4[];
     if (a.stop && *a.stop) return;
     const int q = blockIdx.x, tid = threadIdx.x;
@@ -826,87 +863,111 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
     float4 *Pb = smem4;                                               // [nn][5]
     float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
+    const float4 *hrow_in = reinterpret_cast<const float4 *>(a.h_in);  // rows of 12: h[10], c, 0
     // phase A: projections and coordinates of every needed node
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
-        float h[D];
+        float h[D], cdummy;
+        if (a.first) {
 #pragma unroll
-        for (int o = 0; o < D; ++o) h[o] = a.first ? 0.f : a.h_in[o * a.n_total + node];
+            for (int o = 0; o < D; ++o) h[o] = 0.f;
+        } else {
+            load_hrow(hrow_in, node, h, cdummy);
+        }
         fused_project<T>(W, h, Pb + (size_t)u * 5);
         XY[u] = a.loc_xy[node];
     }
     __syncthreads();
     const int *aptr = a.adj_ptr + a.c_adj_off[q];
     const uint16_t *adj = a.adj + a.c_adj_base[q];
+    const f2_t *Pb2 = reinterpret_cast<const f2_t *>(Pb);  // per node: o01 i01 o23 i23 ...
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int u = p * T + tid;
         if (u >= own) continue;
-        const int node = need[u];
-        float hp[D];  // read again (a cache hit) rather than held across the barrier
-#pragma unroll
-        for (int o = 0; o < D; ++o) hp[o] = a.first ? 0.f : a.h_in[o * a.n_total + node];
-        const int g = a.gid[node];
-        const int j = node - a.loc_ptr[g];
-        const bool inner = j < a.loc_nint[g];
-        const int s0 = a.sub_ptr[g];
-        const double s = a.s[g];
-        float c;
+        const int4 inf = a.info[a.c_n0[q] + u];  // {node, corr index or -1, r index, graph}
+        const int node = inf.x;
+        const bool inner = inf.y >= 0;
+        float hp[D], c;  // read again (a cache hit) rather than held across the barrier
         if (a.first) {
-            c = (inner && s != 0.0) ? (float)(a.r[a.sub_idx[s0 + j]] / s) : 0.f;
-            a.c[node] = c;
+#pragma unroll
+            for (int o = 0; o < D; ++o) hp[o] = 0.f;
+            const double s = a.s[inf.w];
+            c = (inner && s != 0.0) ? (float)(a.r[inf.z] / s) : 0.f;
         } else {
-            c = a.c[node];
+            load_hrow(hrow_in, node, hp, c);
         }
         const float2 xj = XY[u];
-        f2_t pao[D / 2], pai[D / 2], so[D / 2], si[D / 2];
+        const int e0 = aptr[u], e1 = aptr[u + 1];
+        f2_t so[D / 2], si[D / 2];
+        float dout = 0.f;
 #pragma unroll
         for (int m = 0; m < D / 2; ++m) {
-            pao[m] = Wp[F_BA / 2 + m];
-            pai[m] = Wp[(F_BA + D) / 2 + m];
             so[m] = 0ull;
             si[m] = 0ull;
         }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const f2_t xi = f2_pack(hp[i], hp[i]);
-#pragma unroll
-            for (int m = 0; m < D / 2; ++m) {
-                pao[m] = f2_fma(Wp[(F_HA + i * 3 * D) / 2 + m], xi, pao[m]);
-                pai[m] = f2_fma(Wp[(F_HA + i * 3 * D + D) / 2 + m], xi, pai[m]);
-            }
-        }
-        const int e0 = aptr[u], e1 = aptr[u + 1];
-        float dout = 0.f;
-        for (int e = e0; e < e1; ++e) {
-            const unsigned ent = adj[e];
-            const int v = ent & 0x7fffu;
-            const float mo = (float)(ent >> 15);
-            dout += mo;
-            const float2 xl = XY[v];
-            const float dx = xl.x - xj.x, dy = xl.y - xj.y;
-            const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-            const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn), mo2 = f2_pack(mo, mo);
-            const float4 *pb = Pb + (size_t)v * 5;
-            float4 t[D / 2];
-#pragma unroll
-            for (int m = 0; m < D / 2; ++m) t[m] = pb[m];
+        if constexpr (!SPLIT) {
+            f2_t pao[D / 2], pai[D / 2];
 #pragma unroll
             for (int m = 0; m < D / 2; ++m) {
-                f2_t z = f2_add(pao[m], f2_pack(t[m].x, t[m].y));
-                z = f2_fma(Wp[F_WEO / 2 + m], dx2, z);
-                z = f2_fma(Wp[(F_WEO + D) / 2 + m], dy2, z);
-                z = f2_fma(Wp[(F_WEO + 2 * D) / 2 + m], dn2, z);
-                so[m] = f2_fma(f2_relu(z), mo2, so[m]);
+                pao[m] = Wp[F_BA / 2 + m];
+                pai[m] = Wp[(F_BA + D) / 2 + m];
             }
-            if (inner) {
+            f2_mv<F_HA, 3 * D>(pao, Wp, hp);
+            f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
+            for (int e = e0; e < e1; ++e) {
+                const unsigned ent = adj[e];
+                const int v = ent & 0x7fffu;
+                const float mo = (float)(ent >> 15);
+                dout += mo;
+                const float2 xl = XY[v];
+                const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
+                const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn);
+                f2_t po[D / 2], pi[D / 2];
 #pragma unroll
                 for (int m = 0; m < D / 2; ++m) {
-                    f2_t z = f2_add(pai[m], f2_pack(t[m].z, t[m].w));
-                    z = f2_fma(Wp[F_WEI / 2 + m], dx2, z);
-                    z = f2_fma(Wp[(F_WEI + D) / 2 + m], dy2, z);
-                    z = f2_fma(Wp[(F_WEI + 2 * D) / 2 + m], dn2, z);
-                    si[m] = f2_add(si[m], f2_relu(z));
+                    po[m] = Pb2[(size_t)v * 10 + 2 * m];
+                    pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
+                }
+                f2_msg<F_WEO, true>(so, pao, po, Wp, dx2, dy2, dn2, f2_pack(mo, mo));
+                if (inner) f2_msg<F_WEI, false>(si, pai, pi, Wp, dx2, dy2, dn2, 0ull);
+            }
+        } else {
+            {
+                f2_t pao[D / 2];
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) pao[m] = Wp[F_BA / 2 + m];
+                f2_mv<F_HA, 3 * D>(pao, Wp, hp);
+                for (int e = e0; e < e1; ++e) {
+                    const unsigned ent = adj[e];
+                    const int v = ent & 0x7fffu;
+                    const float mo = (float)(ent >> 15);
+                    dout += mo;
+                    const float2 xl = XY[v];
+                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                    const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
+                    f2_t po[D / 2];
+#pragma unroll
+                    for (int m = 0; m < D / 2; ++m) po[m] = Pb2[(size_t)v * 10 + 2 * m];
+                    f2_msg<F_WEO, true>(so, pao, po, Wp, f2_pack(dx, dx), f2_pack(dy, dy), f2_pack(dn, dn),
+                                        f2_pack(mo, mo));
+                }
+            }
+            if (inner) {
+                f2_t pai[D / 2];
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) pai[m] = Wp[(F_BA + D) / 2 + m];
+                f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
+                for (int e = e0; e < e1; ++e) {
+                    const int v = adj[e] & 0x7fffu;
+                    const float2 xl = XY[v];
+                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                    const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
+                    f2_t pi[D / 2];
+#pragma unroll
+                    for (int m = 0; m < D / 2; ++m) pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
+                    f2_msg<F_WEI, false>(si, pai, pi, Wp, f2_pack(dx, dx), f2_pack(dy, dy), f2_pack(dn, dn), 0ull);
                 }
             }
         }
@@ -915,12 +976,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
         f2_t hid[D / 2];
 #pragma unroll
         for (int m = 0; m < D / 2; ++m) hid[m] = Wp[(F_BA + 2 * D) / 2 + m];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const f2_t xi = f2_pack(hp[i], hp[i]);
-#pragma unroll
-            for (int m = 0; m < D / 2; ++m) hid[m] = f2_fma(Wp[(F_HA + i * 3 * D + 2 * D) / 2 + m], xi, hid[m]);
-        }
+        f2_mv<F_HA + 2 * D, 3 * D>(hid, Wp, hp);
         {
             const f2_t cc = f2_pack(c, c), dd = f2_pack(dout, dout), di = f2_pack(din, din);
 #pragma unroll
@@ -930,34 +986,29 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
                 hid[m] = f2_fma(Wp[F_VI / 2 + m], di, hid[m]);
             }
         }
-#pragma unroll
-        for (int i2 = 0; i2 < D / 2; ++i2) {
-            float o0, o1, n0, n1;
-            f2_unpack(so[i2], o0, o1);
-            f2_unpack(si[i2], n0, n1);
-            const f2_t a0 = f2_pack(o0, o0), a1 = f2_pack(o1, o1), b0 = f2_pack(n0, n0), b1 = f2_pack(n1, n1);
+        {
+            float sov[D], siv[D];
 #pragma unroll
             for (int m = 0; m < D / 2; ++m) {
-                hid[m] = f2_fma(Wp[(F_MO + 2 * i2 * D) / 2 + m], a0, hid[m]);
-                hid[m] = f2_fma(Wp[(F_MO + (2 * i2 + 1) * D) / 2 + m], a1, hid[m]);
-                hid[m] = f2_fma(Wp[(F_MI + 2 * i2 * D) / 2 + m], b0, hid[m]);
-                hid[m] = f2_fma(Wp[(F_MI + (2 * i2 + 1) * D) / 2 + m], b1, hid[m]);
+                f2_unpack(so[m], sov[2 * m], sov[2 * m + 1]);
+                f2_unpack(si[m], siv[2 * m], siv[2 * m + 1]);
             }
+            f2_mv<F_MO, D>(hid, Wp, sov);
+            f2_mv<F_MI, D>(hid, Wp, siv);
         }
         // h += alpha (Psi_W2 relu(hid) + Psi_b2)
         f2_t out[D / 2];
-#pragma unroll
-        for (int m = 0; m < D / 2; ++m) out[m] = Wp[F_PB2 / 2 + m];
-#pragma unroll
-        for (int i2 = 0; i2 < D / 2; ++i2) {
-            float r0, r1;
-            f2_unpack(hid[i2], r0, r1);
-            const f2_t a0 = f2_pack(relu(r0), relu(r0)), a1 = f2_pack(relu(r1), relu(r1));
+        {
+            float rh[D];
 #pragma unroll
             for (int m = 0; m < D / 2; ++m) {
-                out[m] = f2_fma(Wp[(F_P2 + 2 * i2 * D) / 2 + m], a0, out[m]);
-                out[m] = f2_fma(Wp[(F_P2 + (2 * i2 + 1) * D) / 2 + m], a1, out[m]);
+                float r0, r1;
+                f2_unpack(hid[m], r0, r1);
+                rh[2 * m] = relu(r0);
+                rh[2 * m + 1] = relu(r1);
+                out[m] = Wp[F_PB2 / 2 + m];
             }
+            f2_mv<F_P2, D>(out, Wp, rh);
         }
         float hn[D];
 #pragma unroll
@@ -970,12 +1021,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
                 f2_t dh[D / 2];
 #pragma unroll
                 for (int m = 0; m < D / 2; ++m) dh[m] = Wp[F_DB1 / 2 + m];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const f2_t xi = f2_pack(hn[i], hn[i]);
-#pragma unroll
-                    for (int m = 0; m < D / 2; ++m) dh[m] = f2_fma(Wp[(F_DW1 + i * D) / 2 + m], xi, dh[m]);
-                }
+                f2_mv<F_DW1, D>(dh, Wp, hn);
                 float y = W.w[F_DB2];
 #pragma unroll
                 for (int m = 0; m < D / 2; ++m) {
@@ -984,11 +1030,14 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
                     y = fmaf(W.w[F_DW2 + 2 * m], relu(d0), y);
                     y = fmaf(W.w[F_DW2 + 2 * m + 1], relu(d1), y);
                 }
-                a.corr[s0 + j] = s == 0.0 ? 0.0 : s * (double)y;
+                const double s = a.s[inf.w];
+                a.corr[inf.y] = s == 0.0 ? 0.0 : s * (double)y;
             }
         } else {
-#pragma unroll
-            for (int o = 0; o < D; ++o) a.h_out[o * a.n_total + node] = hn[o];
+            float4 *hrow_out = reinterpret_cast<float4 *>(a.h_out) + 3 * (size_t)node;
+            hrow_out[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+            hrow_out[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
+            hrow_out[2] = make_float4(hn[8], hn[9], c, 0.f);
         }
     }
 }
@@ -1001,9 +1050,11 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_dss_fused(const __grid
 // adjacency with bit 15 set for neighbours that are unknowns.
 __global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int *c_own, const int *gid,
                                                       const int *loc_ptr, const int *loc_nint, const int *nbr_ptr,
-                                                      const int *nbr_off, const uint16_t *nbr, int pass, int *need_n,
-                                                      int *adj_n, const int *need_off, int *need, const int *adj_off,
-                                                      int *adj_ptr, const int *adj_base, uint16_t *adj, int *st) {
+                                                      const int *nbr_off, const uint16_t *nbr, const int *sub_ptr,
+                                                      const int *sub_idx, int pass, int *need_n, int *adj_n,
+                                                      const int *need_off, int *need, const int *adj_off,
+                                                      int *adj_ptr, const int *adj_base, uint16_t *adj, int4 *info,
+                                                      int *st) {
     constexpr int NT = 256, MAXN = 2048, MAXO = 512;
     __shared__ int cand[MAXN];
     __shared__ int work[MAXO], slot[MAXO], order[MAXO], sptr[MAXO + 1];
@@ -1114,7 +1165,14 @@ __global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int
     int *nd = need + need_off[q];
     int *ap = adj_ptr + adj_off[q];
     uint16_t *ad = adj + adj_base[q];
-    for (int r = threadIdx.x; r < own; r += NT) nd[r] = o0 + order[r];
+    for (int r = threadIdx.x; r < own; r += NT) {
+        const int u = o0 + order[r];
+        const int g = gid[u];
+        const int j = u - loc_ptr[g];
+        const bool in = j < loc_nint[g];
+        nd[r] = u;
+        info[o0 + r] = make_int4(u, in ? sub_ptr[g] + j : -1, in ? sub_idx[sub_ptr[g] + j] : -1, g);
+    }
     for (int t = threadIdx.x; t < ext; t += NT) nd[own + t] = cand[t];
     for (int r = threadIdx.x; r <= own; r += NT) ap[r] = sptr[r];
     for (int r = threadIdx.x; r < own; r += NT) {
@@ -1244,6 +1302,7 @@ void chunk_free(ddg_problem *p) {
     p->chunk.need = p->chunk.c_adj_off = p->chunk.adj_ptr = p->chunk.c_adj_base = nullptr;
     p->chunk.adj = nullptr;
     p->chunk.gid = nullptr;
+    p->chunk.info = nullptr;
     p->chunk.global = false;
     (void)empty;
 }
@@ -1342,27 +1401,33 @@ static int32_t launch_chunks(ddg_problem *p, const ChunkArgs &base, cudaStream_t
     return DDG_OK;
 }
 
-template <int T>
+template <int T, bool SPLIT>
 static int32_t fused_configure() {
     static bool configured = false;
     if (!configured) {
-        DDG_CU(cudaFuncSetAttribute(k_dss_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        DDG_CU(cudaFuncSetAttribute(k_dss_fused<T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024));
         configured = true;
     }
     return DDG_OK;
 }
 
-template <int T>
+template <int T, bool SPLIT>
 static int32_t fused_ctas_per_sm(size_t smem, int *out) {
-    DDG_TRY(fused_configure<T>());
-    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dss_fused<T>, T, smem));
+    DDG_TRY((fused_configure<T, SPLIT>()));
+    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dss_fused<T, SPLIT>, T, smem));
     return DDG_OK;
 }
+
+// schedule-3 variants: chunk width T and whether the edge loop is split (see k_dss_fused)
+static bool fused_split(int variant) { return variant >= 1000; }
+static int fused_T(int variant) { return variant % 1000; }
 
 // Global chunk plan of schedule 3: the concatenated graphs' nodes cut into
 // equal ranges, as many as fill every SM's resident CTAs a whole number of
 // times (at most 2T nodes each), so every SM gets the same work per block.
-int32_t chunk_build_global(ddg_problem *p, int T) {
+int32_t chunk_build_global(ddg_problem *p, int variant) {
+    const int T = fused_T(variant);
     ddg_ctx *c = p->ctx;
     cudaStream_t s = p->stream;
     chunk_free(p);
@@ -1372,11 +1437,12 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     int sms = 0, per_sm = 0;
     DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const size_t smem_est = (size_t)3 * T * (5 * sizeof(float4) + sizeof(float2));  // 2T own + T outside
-    switch (T) {
-        case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
-        case 192: DDG_TRY(fused_ctas_per_sm<192>(smem_est, &per_sm)); break;
-        case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
-        default: set_error("chunk width must be 128, 192 or 256"); return DDG_INVALID_ARG;
+    switch (variant) {
+        case 128: DDG_TRY((fused_ctas_per_sm<128, false>(smem_est, &per_sm))); break;
+        case 256: DDG_TRY((fused_ctas_per_sm<256, false>(smem_est, &per_sm))); break;
+        case 1128: DDG_TRY((fused_ctas_per_sm<128, true>(smem_est, &per_sm))); break;
+        case 1256: DDG_TRY((fused_ctas_per_sm<256, true>(smem_est, &per_sm))); break;
+        default: set_error("schedule-3 variant must be 128, 256, 1128 or 1256"); return DDG_INVALID_ARG;
     }
     const long long slots = (long long)sms * std::max(1, per_sm);
     const long long waves = std::max(1LL, (n + slots * 2 * T - 1) / (slots * 2 * T));
@@ -1391,10 +1457,11 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
         cn0[q] = (int)(q * cs);
         cown[q] = (int)std::min(cs, n - q * cs);
     }
-    cp.T = T;
+    cp.T = variant;
     cp.global = true;
     cp.nchunks = nc;
     DDG_TRY(dalloc(c, cp.allocs, &cp.gid, n));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.info, n));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_n0, nc));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_own, nc));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_off, nc));
@@ -1407,8 +1474,8 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     int *adj_n = nullptr;
     DDG_CU(cudaMallocAsync(&adj_n, sizeof(int) * nc, s));
     k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
-                                      p->nbr, 0, cp.c_need_n, adj_n, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                      nullptr, p->d_status);
+                                      p->nbr, p->sub_ptr, p->sub_idx, 0, cp.c_need_n, adj_n, nullptr, nullptr,
+                                      nullptr, nullptr, nullptr, nullptr, nullptr, p->d_status);
     DDG_LAUNCH_CHECK();
     std::vector<int> hn(nc), ha(nc);
     DDG_CU(cudaMemcpyAsync(hn.data(), cp.c_need_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
@@ -1435,17 +1502,17 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     DDG_CU(cudaMemcpyAsync(cp.c_adj_off, aoff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_adj_base, abase.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
-                                      p->nbr, 1, nullptr, nullptr, cp.c_need_off, cp.need, cp.c_adj_off, cp.adj_ptr,
-                                      cp.c_adj_base, cp.adj, p->d_status);
+                                      p->nbr, p->sub_ptr, p->sub_idx, 1, nullptr, nullptr, cp.c_need_off, cp.need,
+                                      cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->d_status);
     DDG_LAUNCH_CHECK();
     DDG_CU(cudaFreeAsync(adj_n, s));
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
 }
 
-template <int T>
+template <int T, bool SPLIT>
 static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t s) {
-    DDG_TRY(fused_configure<T>());
+    DDG_TRY((fused_configure<T, SPLIT>()));
     const ddg_model *m = p->model;
     const size_t smem = (size_t)p->chunk.max_need * (5 * sizeof(float4) + sizeof(float2));
     if (smem > 227 * 1024) {
@@ -1459,7 +1526,7 @@ static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t 
         a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
         a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
         const FusedWeights *W = reinterpret_cast<const FusedWeights *>(w_fused_host(p)) + blk;
-        k_dss_fused<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
+        k_dss_fused<T, SPLIT><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
     }
     DDG_LAUNCHES(m->kbar);
     return DDG_OK;
@@ -1481,6 +1548,7 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.loc_ptr = p->loc_ptr;
     a.loc_nint = p->loc_nint;
     a.gid = cp.gid;
+    a.info = cp.info;
     a.sub_ptr = p->sub_ptr;
     a.sub_idx = p->sub_idx;
     a.loc_xy = p->loc_xy;
@@ -1493,9 +1561,10 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.stop = stop;
     if (cp.global) {
         switch (cp.T) {
-            case 128: return launch_fused<128>(p, a, s);
-            case 192: return launch_fused<192>(p, a, s);
-            case 256: return launch_fused<256>(p, a, s);
+            case 128: return launch_fused<128, false>(p, a, s);
+            case 256: return launch_fused<256, false>(p, a, s);
+            case 1128: return launch_fused<128, true>(p, a, s);
+            case 1256: return launch_fused<256, true>(p, a, s);
             default: set_error("no chunk plan"); return DDG_INVALID_ARG;
         }
     }

@@ -114,7 +114,9 @@ def test_autograd_function_trains_through_the_hand_written_backward():
         loss.backward()
         l_ref, g_ref = ddg.ddg_train_loss_grad(p, m, rd, graphs, W0.size)
         assert float(loss) == l_ref
-        assert np.array_equal(wt.grad.cpu().numpy(), g_ref)
+        # weight gradients are summed with float atomics across CTAs: equal up to summation order
+        g = wt.grad.cpu().numpy()
+        assert np.allclose(g, g_ref, rtol=1e-4, atol=1e-6 * np.abs(g_ref).max())
         assert np.array_equal(ddg.ddg_model_get_weights(m, W0.size), W0)
         opt = torch.optim.Adam([wt], lr=1e-3)
         first = float(loss)
