@@ -1419,8 +1419,7 @@ static int32_t fused_ctas_per_sm(size_t smem, int *out) {
     return DDG_OK;
 }
 
-// schedule-3 variants: chunk width T and whether the edge loop is split (see k_dss_fused)
-static bool fused_split(int variant) { return variant >= 1000; }
+// schedule-3 variant: chunk width T, plus 1000 when the edge loop is split (see k_dss_fused)
 static int fused_T(int variant) { return variant % 1000; }
 
 // Global chunk plan of schedule 3: the concatenated graphs' nodes cut into
