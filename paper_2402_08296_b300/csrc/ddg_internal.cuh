@@ -105,6 +105,7 @@ struct ddg_model {
 // chunked GNN schedule: graphs cut into chunks of at most 2 * T nodes (see dss.cu)
 struct ChunkPlan {
     int T = 0, nchunks = 0, max_need = 0;
+    size_t max_smem = 0;  // schedule 3: largest per-CTA shared memory of the plan
     bool global = false;  // schedule 3: chunks are ranges of the concatenated graphs' nodes, sized to fill
                           // the GPU evenly; own nodes sorted by message count, neighbour kind in bit 15
     int *gid = nullptr;   // global: graph of every local node (sum_loc)
@@ -235,7 +236,7 @@ int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaSt
 int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
 int32_t chunk_build(ddg_problem *p, int T);
-int32_t chunk_build_global(ddg_problem *p, int variant);  // variant: chunk width (+1000: split edge loop)
+int32_t chunk_build_global(ddg_problem *p, int T);
 void chunk_free(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);

@@ -849,10 +849,23 @@ __device__ __forceinline__ void f2_msg(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 
     }
 }
 
-// SPLIT runs the out- and in-messages in two passes over the neighbours (recomputing the
-// edge geometry) so that fewer accumulators are live at once: fewer registers, more warps.
-template <int T, bool SPLIT>
-__global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
+// shared-memory carve-up of one chunk: projections, coordinates, own-node records,
+// adjacency offsets and the adjacency itself (byte offsets, 16-byte aligned starts)
+struct FusedSmem {
+    size_t xy, info, aptr, adj, total;
+};
+__host__ __device__ __forceinline__ FusedSmem fused_smem(int nn, int own, int nadj) {
+    FusedSmem m;
+    m.xy = (size_t)nn * 5 * sizeof(float4);
+    m.info = (m.xy + (size_t)nn * sizeof(float2) + 15) & ~(size_t)15;
+    m.aptr = m.info + (size_t)own * sizeof(int4);
+    m.adj = m.aptr + (size_t)(own + 1) * sizeof(int);
+    m.total = (m.adj + (size_t)nadj * sizeof(uint16_t) + 15) & ~(size_t)15;
+    return m;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 128))
     k_dss_fused(const __grid_constant__ FusedWeights W, const __grid_constant__ ChunkArgs a) {
     extern __shared__ __align__(16) float4 smem4[];
     if (a.stop && *a.stop) return;
@@ -860,11 +873,23 @@ __global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
     const int own = a.c_own[q];
     const int nn = a.c_need_n[q];
     const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
-    float4 *Pb = smem4;                                               // [nn][5]
-    float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
+    const int *aptr_g = a.adj_ptr + a.c_adj_off[q];
+    const uint16_t *adj_g = a.adj + a.c_adj_base[q];
+    const int4 *info_g = a.info + a.c_n0[q];
+    const int nadj = aptr_g[own];
+    const FusedSmem L = fused_smem(nn, own, nadj);
+    char *sm = reinterpret_cast<char *>(smem4);
+    float4 *Pb = smem4;                                      // [nn][5]
+    float2 *XY = reinterpret_cast<float2 *>(sm + L.xy);      // [nn]
+    int4 *INFO = reinterpret_cast<int4 *>(sm + L.info);      // [own] {node, corr idx, r idx, graph}
+    int *APTR = reinterpret_cast<int *>(sm + L.aptr);        // [own + 1]
+    uint16_t *ADJ = reinterpret_cast<uint16_t *>(sm + L.adj);  // [nadj]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     const float4 *hrow_in = reinterpret_cast<const float4 *>(a.h_in);  // rows of 12: h[10], c, 0
-    // phase A: projections and coordinates of every needed node
+    // phase A: stage the chunk's records and adjacency; projections and coordinates of every needed node
+    for (int i = tid; i < own; i += T) INFO[i] = info_g[i];
+    for (int i = tid; i <= own; i += T) APTR[i] = aptr_g[i];
+    for (int i = tid; i < nadj; i += T) ADJ[i] = adj_g[i];
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
         float h[D], cdummy;
@@ -878,14 +903,12 @@ __global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
         XY[u] = a.loc_xy[node];
     }
     __syncthreads();
-    const int *aptr = a.adj_ptr + a.c_adj_off[q];
-    const uint16_t *adj = a.adj + a.c_adj_base[q];
     const f2_t *Pb2 = reinterpret_cast<const f2_t *>(Pb);  // per node: o01 i01 o23 i23 ...
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int u = p * T + tid;
         if (u >= own) continue;
-        const int4 inf = a.info[a.c_n0[q] + u];  // {node, corr index or -1, r index, graph}
+        const int4 inf = INFO[u];
         const int node = inf.x;
         const bool inner = inf.y >= 0;
         float hp[D], c;  // read again (a cache hit) rather than held across the barrier
@@ -898,78 +921,35 @@ __global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
             load_hrow(hrow_in, node, hp, c);
         }
         const float2 xj = XY[u];
-        const int e0 = aptr[u], e1 = aptr[u + 1];
-        f2_t so[D / 2], si[D / 2];
+        const int e0 = APTR[u], e1 = APTR[u + 1];
+        f2_t so[D / 2], si[D / 2], pao[D / 2], pai[D / 2];
         float dout = 0.f;
 #pragma unroll
         for (int m = 0; m < D / 2; ++m) {
             so[m] = 0ull;
             si[m] = 0ull;
+            pao[m] = Wp[F_BA / 2 + m];
+            pai[m] = Wp[(F_BA + D) / 2 + m];
         }
-        if constexpr (!SPLIT) {
-            f2_t pao[D / 2], pai[D / 2];
+        f2_mv<F_HA, 3 * D>(pao, Wp, hp);
+        if (inner) f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
+        for (int e = e0; e < e1; ++e) {
+            const unsigned ent = ADJ[e];
+            const int v = ent & 0x7fffu;
+            const float mo = (float)(ent >> 15);
+            dout += mo;
+            const float2 xl = XY[v];
+            const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+            const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
+            const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn);
+            f2_t po[D / 2], pi[D / 2];
 #pragma unroll
             for (int m = 0; m < D / 2; ++m) {
-                pao[m] = Wp[F_BA / 2 + m];
-                pai[m] = Wp[(F_BA + D) / 2 + m];
+                po[m] = Pb2[(size_t)v * 10 + 2 * m];
+                pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
             }
-            f2_mv<F_HA, 3 * D>(pao, Wp, hp);
-            f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
-            for (int e = e0; e < e1; ++e) {
-                const unsigned ent = adj[e];
-                const int v = ent & 0x7fffu;
-                const float mo = (float)(ent >> 15);
-                dout += mo;
-                const float2 xl = XY[v];
-                const float dx = xl.x - xj.x, dy = xl.y - xj.y;
-                const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-                const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn);
-                f2_t po[D / 2], pi[D / 2];
-#pragma unroll
-                for (int m = 0; m < D / 2; ++m) {
-                    po[m] = Pb2[(size_t)v * 10 + 2 * m];
-                    pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
-                }
-                f2_msg<F_WEO, true>(so, pao, po, Wp, dx2, dy2, dn2, f2_pack(mo, mo));
-                if (inner) f2_msg<F_WEI, false>(si, pai, pi, Wp, dx2, dy2, dn2, 0ull);
-            }
-        } else {
-            {
-                f2_t pao[D / 2];
-#pragma unroll
-                for (int m = 0; m < D / 2; ++m) pao[m] = Wp[F_BA / 2 + m];
-                f2_mv<F_HA, 3 * D>(pao, Wp, hp);
-                for (int e = e0; e < e1; ++e) {
-                    const unsigned ent = adj[e];
-                    const int v = ent & 0x7fffu;
-                    const float mo = (float)(ent >> 15);
-                    dout += mo;
-                    const float2 xl = XY[v];
-                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
-                    const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-                    f2_t po[D / 2];
-#pragma unroll
-                    for (int m = 0; m < D / 2; ++m) po[m] = Pb2[(size_t)v * 10 + 2 * m];
-                    f2_msg<F_WEO, true>(so, pao, po, Wp, f2_pack(dx, dx), f2_pack(dy, dy), f2_pack(dn, dn),
-                                        f2_pack(mo, mo));
-                }
-            }
-            if (inner) {
-                f2_t pai[D / 2];
-#pragma unroll
-                for (int m = 0; m < D / 2; ++m) pai[m] = Wp[(F_BA + D) / 2 + m];
-                f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
-                for (int e = e0; e < e1; ++e) {
-                    const int v = adj[e] & 0x7fffu;
-                    const float2 xl = XY[v];
-                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
-                    const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-                    f2_t pi[D / 2];
-#pragma unroll
-                    for (int m = 0; m < D / 2; ++m) pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
-                    f2_msg<F_WEI, false>(si, pai, pi, Wp, f2_pack(dx, dx), f2_pack(dy, dy), f2_pack(dn, dn), 0ull);
-                }
-            }
+            f2_msg<F_WEO, true>(so, pao, po, Wp, dx2, dy2, dn2, f2_pack(mo, mo));
+            if (inner) f2_msg<F_WEI, false>(si, pai, pi, Wp, dx2, dy2, dn2, 0ull);
         }
         const float din = inner ? (float)(e1 - e0) : 0.f;
         // Psi hidden layer on [h, c, phi_out, phi_in] with the second message layers composed in
@@ -994,7 +974,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * (SPLIT ? 96 : 128)))
                 f2_unpack(si[m], siv[2 * m], siv[2 * m + 1]);
             }
             f2_mv<F_MO, D>(hid, Wp, sov);
-            f2_mv<F_MI, D>(hid, Wp, siv);
+            if (inner) f2_mv<F_MI, D>(hid, Wp, siv);
         }
         // h += alpha (Psi_W2 relu(hid) + Psi_b2)
         f2_t out[D / 2];
@@ -1401,32 +1381,27 @@ static int32_t launch_chunks(ddg_problem *p, const ChunkArgs &base, cudaStream_t
     return DDG_OK;
 }
 
-template <int T, bool SPLIT>
+template <int T>
 static int32_t fused_configure() {
     static bool configured = false;
     if (!configured) {
-        DDG_CU(cudaFuncSetAttribute(k_dss_fused<T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    227 * 1024));
+        DDG_CU(cudaFuncSetAttribute(k_dss_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         configured = true;
     }
     return DDG_OK;
 }
 
-template <int T, bool SPLIT>
+template <int T>
 static int32_t fused_ctas_per_sm(size_t smem, int *out) {
-    DDG_TRY((fused_configure<T, SPLIT>()));
-    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dss_fused<T, SPLIT>, T, smem));
+    DDG_TRY(fused_configure<T>());
+    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_dss_fused<T>, T, smem));
     return DDG_OK;
 }
-
-// schedule-3 variant: chunk width T, plus 1000 when the edge loop is split (see k_dss_fused)
-static int fused_T(int variant) { return variant % 1000; }
 
 // Global chunk plan of schedule 3: the concatenated graphs' nodes cut into
 // equal ranges, as many as fill every SM's resident CTAs a whole number of
 // times (at most 2T nodes each), so every SM gets the same work per block.
-int32_t chunk_build_global(ddg_problem *p, int variant) {
-    const int T = fused_T(variant);
+int32_t chunk_build_global(ddg_problem *p, int T) {
     ddg_ctx *c = p->ctx;
     cudaStream_t s = p->stream;
     chunk_free(p);
@@ -1435,13 +1410,11 @@ int32_t chunk_build_global(ddg_problem *p, int variant) {
     const int K = p->K;
     int sms = 0, per_sm = 0;
     DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t smem_est = (size_t)3 * T * (5 * sizeof(float4) + sizeof(float2));  // 2T own + T outside
-    switch (variant) {
-        case 128: DDG_TRY((fused_ctas_per_sm<128, false>(smem_est, &per_sm))); break;
-        case 256: DDG_TRY((fused_ctas_per_sm<256, false>(smem_est, &per_sm))); break;
-        case 1128: DDG_TRY((fused_ctas_per_sm<128, true>(smem_est, &per_sm))); break;
-        case 1256: DDG_TRY((fused_ctas_per_sm<256, true>(smem_est, &per_sm))); break;
-        default: set_error("schedule-3 variant must be 128, 256, 1128 or 1256"); return DDG_INVALID_ARG;
+    const size_t smem_est = fused_smem(3 * T, 2 * T, 14 * T).total;  // 2T own + T outside, degree 7
+    switch (T) {
+        case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
+        case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
+        default: set_error("schedule-3 chunk width must be 128 or 256"); return DDG_INVALID_ARG;
     }
     const long long slots = (long long)sms * std::max(1, per_sm);
     const long long waves = std::max(1LL, (n + slots * 2 * T - 1) / (slots * 2 * T));
@@ -1456,7 +1429,7 @@ int32_t chunk_build_global(ddg_problem *p, int variant) {
         cn0[q] = (int)(q * cs);
         cown[q] = (int)std::min(cs, n - q * cs);
     }
-    cp.T = variant;
+    cp.T = T;
     cp.global = true;
     cp.nchunks = nc;
     DDG_TRY(dalloc(c, cp.allocs, &cp.gid, n));
@@ -1484,6 +1457,7 @@ int32_t chunk_build_global(ddg_problem *p, int variant) {
     std::vector<int> noff(nc), aoff(nc), abase(nc);
     long long tn = 0, ta = 0, tp = 0;
     int maxn = 0;
+    size_t max_smem = 0;
     for (int q = 0; q < nc; ++q) {
         noff[q] = (int)tn;
         abase[q] = (int)ta;
@@ -1492,8 +1466,14 @@ int32_t chunk_build_global(ddg_problem *p, int variant) {
         ta += ha[q];
         tp += cown[q] + 1;
         maxn = std::max(maxn, hn[q]);
+        max_smem = std::max(max_smem, fused_smem(hn[q], cown[q], ha[q]).total);
     }
     cp.max_need = maxn;
+    cp.max_smem = max_smem;
+    if (max_smem > 227 * 1024) {
+        set_error("a GNN chunk needs more shared memory than a CTA has");
+        return DDG_TOO_LARGE;
+    }
     DDG_TRY(dalloc(c, cp.allocs, &cp.need, tn));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj, ta));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj_ptr, tp));
@@ -1509,15 +1489,11 @@ int32_t chunk_build_global(ddg_problem *p, int variant) {
     return check_status(p, "GNN chunks");
 }
 
-template <int T, bool SPLIT>
+template <int T>
 static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t s) {
-    DDG_TRY((fused_configure<T, SPLIT>()));
+    DDG_TRY(fused_configure<T>());
     const ddg_model *m = p->model;
-    const size_t smem = (size_t)p->chunk.max_need * (5 * sizeof(float4) + sizeof(float2));
-    if (smem > 227 * 1024) {
-        set_error("a GNN chunk needs more shared memory than a CTA has");
-        return DDG_TOO_LARGE;
-    }
+    const size_t smem = p->chunk.max_smem;
     for (int blk = 0; blk < m->kbar; ++blk) {
         ChunkArgs a = base;
         a.first = blk == 0;
@@ -1525,7 +1501,7 @@ static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t 
         a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
         a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
         const FusedWeights *W = reinterpret_cast<const FusedWeights *>(w_fused_host(p)) + blk;
-        k_dss_fused<T, SPLIT><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
+        k_dss_fused<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
     }
     DDG_LAUNCHES(m->kbar);
     return DDG_OK;
@@ -1560,10 +1536,8 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.stop = stop;
     if (cp.global) {
         switch (cp.T) {
-            case 128: return launch_fused<128, false>(p, a, s);
-            case 256: return launch_fused<256, false>(p, a, s);
-            case 1128: return launch_fused<128, true>(p, a, s);
-            case 1256: return launch_fused<256, true>(p, a, s);
+            case 128: return launch_fused<128>(p, a, s);
+            case 256: return launch_fused<256>(p, a, s);
             default: set_error("no chunk plan"); return DDG_INVALID_ARG;
         }
     }

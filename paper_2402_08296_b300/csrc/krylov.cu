@@ -194,8 +194,8 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 // per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
 // the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256); 3 = the
 // chunks of 2 with composed weights, packed two-lane FP32 and message-sorted nodes.
-// DDG_GNN_SCHEDULE = 0..3 (and DDG_GNN_CHUNK_T = 128/192/256, for schedule 3
-// 128/256 or 1128/1256 with the split edge loop) forces one.
+// DDG_GNN_SCHEDULE = 0..3 (and DDG_GNN_CHUNK_T = 128/192/256 for schedule 2,
+// 128/256 for schedule 3) forces one.
 // The choice is cached in the context per decomposition shape class, so a stream
 // of requests of similar sizes tunes once.
 int32_t dss_autotune(ddg_problem *p) {
@@ -237,8 +237,7 @@ int32_t dss_autotune(ddg_problem *p) {
     DDG_CU(cudaEventCreate(&e1));
     float best = 1e30f;
     int pick = 0, pickT = 0;
-    // schedule 3's second field: chunk width, plus 1000 for the split edge loop
-    const int cands[9][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}, {3, 128}, {3, 256}, {3, 1128}, {3, 1256}};
+    const int cands[7][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}, {3, 128}, {3, 256}};
     for (const auto &cd : cands) {
         if (cd[0] < 2 && !p->dss_whole_graph) continue;
         p->dss_sched = cd[0];

@@ -112,8 +112,7 @@ def test_dss_local_corrections(ddg, ctx, torch, name, seed, K, delta, alpha, bia
         ddg.ddg_model_destroy(m)
 
 
-@pytest.mark.parametrize("schedule,chunk_t", [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256"),
-                                              ("3", "1128")])
+@pytest.mark.parametrize("schedule,chunk_t", [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256")])
 def test_dss_local_corrections_every_schedule(ddg, ctx, torch, schedule, chunk_t, monkeypatch):
     """Every GNN schedule against the FP64 oracle on ragged ~1,300-node graphs; with
     T = 128 each graph spans several chunks, so chunk borders and halos are exercised."""
