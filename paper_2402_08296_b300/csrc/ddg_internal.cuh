@@ -151,6 +151,7 @@ struct ddg_problem {
     int *part = nullptr;                     // [nf]
     int *mem_ptr = nullptr, *mem_idx = nullptr; // node -> subdomains (ascending)
     int *mult = nullptr;                     // [nf]
+    double *inv_mult = nullptr;              // [nf] 1 / mult
     int *sub_ptr = nullptr, *sub_idx = nullptr; // subdomain -> free ids (ascending)
     int *inv_pos = nullptr;                  // mem slot -> position in sub_idx
     long long sum_k = 0;

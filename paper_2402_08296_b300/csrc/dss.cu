@@ -849,19 +849,10 @@ __device__ __forceinline__ void f2_msg(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 
     }
 }
 
-// shared-memory carve-up of one chunk: projections, coordinates, own-node records,
-// adjacency offsets and the adjacency itself (byte offsets, 16-byte aligned starts)
-struct FusedSmem {
-    size_t xy, info, aptr, adj, total;
-};
-__host__ __device__ __forceinline__ FusedSmem fused_smem(int nn, int own, int nadj) {
-    FusedSmem m;
-    m.xy = (size_t)nn * 5 * sizeof(float4);
-    m.info = (m.xy + (size_t)nn * sizeof(float2) + 15) & ~(size_t)15;
-    m.aptr = m.info + (size_t)own * sizeof(int4);
-    m.adj = m.aptr + (size_t)(own + 1) * sizeof(int);
-    m.total = (m.adj + (size_t)nadj * sizeof(uint16_t) + 15) & ~(size_t)15;
-    return m;
+// shared memory of one chunk: the neighbour projections (five float4) and the
+// scaled coordinates (float2) of each of its nn needed nodes
+__host__ __device__ __forceinline__ size_t fused_smem(int nn) {
+    return (size_t)nn * (5 * sizeof(float4) + sizeof(float2));
 }
 
 template <int T>
@@ -873,23 +864,14 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
     const int own = a.c_own[q];
     const int nn = a.c_need_n[q];
     const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
-    const int *aptr_g = a.adj_ptr + a.c_adj_off[q];
-    const uint16_t *adj_g = a.adj + a.c_adj_base[q];
-    const int4 *info_g = a.info + a.c_n0[q];
-    const int nadj = aptr_g[own];
-    const FusedSmem L = fused_smem(nn, own, nadj);
-    char *sm = reinterpret_cast<char *>(smem4);
-    float4 *Pb = smem4;                                      // [nn][5]
-    float2 *XY = reinterpret_cast<float2 *>(sm + L.xy);      // [nn]
-    int4 *INFO = reinterpret_cast<int4 *>(sm + L.info);      // [own] {node, corr idx, r idx, graph}
-    int *APTR = reinterpret_cast<int *>(sm + L.aptr);        // [own + 1]
-    uint16_t *ADJ = reinterpret_cast<uint16_t *>(sm + L.adj);  // [nadj]
+    const int *APTR = a.adj_ptr + a.c_adj_off[q];      // [own + 1]
+    const uint16_t *ADJ = a.adj + a.c_adj_base[q];     // chunk-local ids, bit 15: neighbour is an unknown
+    const int4 *INFO = a.info + a.c_n0[q];             // [own] {node, corr idx, r idx, graph}
+    float4 *Pb = smem4;                                               // [nn][5]
+    float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     const float4 *hrow_in = reinterpret_cast<const float4 *>(a.h_in);  // rows of 12: h[10], c, 0
-    // phase A: stage the chunk's records and adjacency; projections and coordinates of every needed node
-    for (int i = tid; i < own; i += T) INFO[i] = info_g[i];
-    for (int i = tid; i <= own; i += T) APTR[i] = aptr_g[i];
-    for (int i = tid; i < nadj; i += T) ADJ[i] = adj_g[i];
+    // phase A: projections and coordinates of every needed node
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
         float h[D], cdummy;
@@ -1410,7 +1392,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     const int K = p->K;
     int sms = 0, per_sm = 0;
     DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t smem_est = fused_smem(3 * T, 2 * T, 14 * T).total;  // 2T own + T outside, degree 7
+    const size_t smem_est = fused_smem(3 * T);  // 2T own + T outside nodes
     switch (T) {
         case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
         case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
@@ -1418,7 +1400,9 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     }
     const long long slots = (long long)sms * std::max(1, per_sm);
     const long long waves = std::max(1LL, (n + slots * 2 * T - 1) / (slots * 2 * T));
-    const long long cs = (n + slots * waves - 1) / (slots * waves);
+    // at least one node per thread: a small problem takes fewer CTAs (and leaves SMs to the
+    // kernels of other streams) rather than slivers of a few nodes with large halos
+    const long long cs = std::max<long long>(T, (n + slots * waves - 1) / (slots * waves));
     const int nc = (int)((n + cs - 1) / cs);
     std::vector<int> lp(K + 1), gid(n), cn0(nc), cown(nc);
     DDG_CU(cudaMemcpyAsync(lp.data(), p->loc_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
@@ -1466,7 +1450,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
         ta += ha[q];
         tp += cown[q] + 1;
         maxn = std::max(maxn, hn[q]);
-        max_smem = std::max(max_smem, fused_smem(hn[q], cown[q], ha[q]).total);
+        max_smem = std::max(max_smem, fused_smem(hn[q]));
     }
     cp.max_need = maxn;
     cp.max_smem = max_smem;

@@ -24,7 +24,8 @@
 namespace ddg {
 
 constexpr int KT = 256;            // threads per block of the vector kernels
-constexpr int RB = 296;            // fixed grid of the reductions (2 x 148 SMs)
+constexpr int RB = 1184;           // fixed grid of the streaming kernels: 8 CTAs of 256 on each of 148 SMs
+constexpr int LPR = 8;             // lanes per CSR row in the SpMV
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
@@ -34,42 +35,41 @@ enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT
 enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
 
 // ------------------------------------------------------------------ SpMV
+// y_i = sum_e val[e] x[col[e]] with LPR lanes per row: a row's entries are read by
+// consecutive lanes (coalesced), then summed by a fixed shuffle tree.  Every lane of
+// the warp calls it (rows i >= n contribute nothing), so the full-warp shuffles are
+// always executed by all 32 lanes.  Returns the row's value in every lane of its group.
+__device__ __forceinline__ double csr_row(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                          const double *__restrict__ val, const double *__restrict__ x, int i,
+                                          int n, int sub) {
+    double acc = 0.0;
+    const int e0 = i < n ? rowptr[i] + sub : 0, e1 = i < n ? rowptr[i + 1] : 0;
+    for (int e = e0; e < e1; e += LPR) acc += val[e] * x[col[e]];
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LPR);
+    return acc;
+}
+
 __global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
                                              const double *__restrict__ val, const double *__restrict__ x,
-                                             double *__restrict__ y, int n, const double *__restrict__ rdot,
-                                             double *part, const int *stop) {
-    __shared__ double sh[32];
-    if (stop && *stop) return;
-    int i = blockIdx.x * KT + threadIdx.x;
-    double pq = 0.0, pr = 0.0;
-    if (i < n) {
-        double acc = 0.0;
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * x[col[e]];
-        y[i] = acc;
-        if (part) {
-            double xi = x[i];
-            pq = xi * acc;
-            pr = xi * rdot[i];
-        }
-    }
-    if (part) {
-        pq = block_sum(pq, sh);
-        pr = block_sum(pr, sh);
-        if (threadIdx.x == 0) {
-            part[blockIdx.x] = pq;
-            part[gridDim.x + blockIdx.x] = pr;
-        }
+                                             double *__restrict__ y, int n) {
+    const int sub = threadIdx.x % LPR;
+    const int rows_per_grid = gridDim.x * (KT / LPR);
+    for (int i0 = blockIdx.x * (KT / LPR); i0 < n; i0 += rows_per_grid) {  // uniform over the block
+        const int i = i0 + threadIdx.x / LPR;
+        const double acc = csr_row(rowptr, col, val, x, i, n, sub);
+        if (sub == 0 && i < n) y[i] = acc;
     }
 }
 
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
-    k_spmv<<<cdiv(p->nf, KT), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf, nullptr, nullptr, nullptr);
+    k_spmv<<<std::min(RB, cdiv(p->nf, KT / LPR)), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf);
     DDG_LAUNCH_CHECK();
     return DDG_OK;
 }
 
 // ------------------------------------------------------------------ preconditioner pieces
-__global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *sub_idx, const int *mult,
+__global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *sub_idx, const double *inv_mult,
                                                  const double *r, double *s_out, double *y_out, const int *stop) {
     __shared__ double sh[32];
     if (stop && *stop) return;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *
         int j = sub_idx[q];
         double v = r[j];
         ss += v * v;
-        yy += v * (1.0 / mult[j]);
+        yy += v * inv_mult[j];
     }
     ss = block_sum(ss, sh);
     yy = block_sum(yy, sh);
@@ -103,12 +103,12 @@ __global__ void k_coarse_gemv(const double *Ainv, const double *y, double *w, in
 }
 
 __global__ void __launch_bounds__(KT) k_prolong(const int *mptr, const int *midx, const int *inv_pos,
-                                                const int *mult, const double *corr, const double *w, int nf,
+                                                const double *inv_mult, const double *corr, const double *w, int nf,
                                                 int coarse, int pou, double *z, const int *stop) {
     if (stop && *stop) return;
     int j = blockIdx.x * KT + threadIdx.x;
     if (j >= nf) return;
-    double inv_m = 1.0 / mult[j];
+    const double inv_m = inv_mult[j];
     double acc = 0.0;
     int q0 = mptr[j], q1 = mptr[j + 1];
     if (coarse)
@@ -151,7 +151,7 @@ static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStre
         return DDG_OK;
     }
     const int K = p->K;
-    k_restrict<<<K, KT, 0, s>>>(p->sub_ptr, p->sub_idx, p->mult, r, p->s, p->y, stop);
+    k_restrict<<<K, KT, 0, s>>>(p->sub_ptr, p->sub_idx, p->inv_mult, r, p->s, p->y, stop);
     DDG_LAUNCH_CHECK();
     ++nl;
     const bool coarse = (p->flags & DDG_COARSE) != 0;
@@ -169,7 +169,7 @@ static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStre
     if (ev_local) DDG_CU(record_event(ev_local[1], s));
     ++nl;
     if (prolong) {
-        k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->mult, p->corr, p->wc,
+        k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->inv_mult, p->corr, p->wc,
                                                  p->nf, coarse ? 1 : 0, (p->flags & DDG_POU_PROLONG) ? 1 : 0, z,
                                                  stop);
         DDG_LAUNCH_CHECK();
@@ -295,6 +295,13 @@ __device__ __forceinline__ bool last_block(int *ticket) {
     return is_last;
 }
 
+// sum of part[0..n) by the whole block in a fixed order (valid in thread 0)
+__device__ __forceinline__ double block_sum_parts(const double *part, int n, double *sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
+    return block_sum(v, sh);
+}
+
 // sum of part[0..n) by one warp in a fixed order (valid in every lane)
 __device__ __forceinline__ double warp_sum_parts(const double *part, int n, int lane) {
     double v = 0.0;
@@ -312,8 +319,8 @@ __global__ void __launch_bounds__(KT) k_dot(const double *a, const double *b, in
 }
 
 // d_j = z . Q[slot_j]; the last block forms beta_j = d_j / (p_j . q_j)
-__global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *Q, long long ld, Window win, int n,
-                                                 double *part, double *scal, int *flag) {
+__global__ void __launch_bounds__(KT, 4) k_multidot(const double *z, const double *Q, long long ld, Window win, int n,
+                                                    double *part, double *scal, int *flag) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
     double acc[MAXM];
@@ -325,9 +332,12 @@ __global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *
         for (int j = 0; j < MAXM; ++j)
             if (j < win.W) acc[j] += zi * Q[win.slot[j] * ld + i];
     }
-    for (int j = 0; j < win.W; ++j) {
-        double v = block_sum(acc[j], sh);
-        if (threadIdx.x == 0) part[j * RB + blockIdx.x] = v;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {  // static indices keep acc[] in registers
+        if (j < win.W) {
+            double v = block_sum(acc[j], sh);
+            if (threadIdx.x == 0) part[j * RB + blockIdx.x] = v;
+        }
     }
     if (last_block(&flag[F_T_MD])) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -340,8 +350,8 @@ __global__ void __launch_bounds__(KT) k_multidot(const double *z, const double *
 }
 
 // P[snew] = z - sum_j beta_j P[slot_j]  (P[snew] may be one of the P[slot_j]: read before write, same index)
-__global__ void __launch_bounds__(KT) k_pupdate(const double *z, double *P, long long ld, Window win, int n,
-                                                const double *scal, const int *flag) {
+__global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, long long ld, Window win, int n,
+                                                   const double *scal, const int *flag) {
     if (flag[F_STOP]) return;
     __shared__ double beta[MAXM];
     if (threadIdx.x < MAXM) beta[threadIdx.x] = threadIdx.x < win.W ? scal[S_BETA + threadIdx.x] : 0.0;
@@ -355,22 +365,26 @@ __global__ void __launch_bounds__(KT) k_pupdate(const double *z, double *P, long
     }
 }
 
-// q = A p with the partial dots p.q and p.r; the last block forms alpha = (p.r) / (p.q)
+// q = A p with the partial dots p.q and p.r (LPR lanes per row, fixed grid of RB
+// blocks striding over the rows); the last block forms alpha = (p.r) / (p.q)
 __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
                                                  const double *__restrict__ val, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
                                                  double *part, Window win, double *scal, int *flag) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
-    int i = blockIdx.x * KT + threadIdx.x;
+    const int sub = threadIdx.x % LPR;
+    const int rows_per_grid = gridDim.x * (KT / LPR);
     double pq = 0.0, pr = 0.0;
-    if (i < n) {
-        double acc = 0.0;
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * p[col[e]];
-        q[i] = acc;
-        double pi = p[i];
-        pq = pi * acc;
-        pr = pi * r[i];
+    for (int i0 = blockIdx.x * (KT / LPR); i0 < n; i0 += rows_per_grid) {  // uniform over the block
+        const int i = i0 + threadIdx.x / LPR;
+        const double acc = csr_row(rowptr, col, val, p, i, n, sub);
+        if (sub == 0 && i < n) {
+            q[i] = acc;
+            const double pi = p[i];
+            pq += pi * acc;
+            pr += pi * r[i];
+        }
     }
     pq = block_sum(pq, sh);
     pr = block_sum(pr, sh);
@@ -379,16 +393,10 @@ __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr,
         part[gridDim.x + blockIdx.x] = pr;
     }
     if (last_block(&flag[F_T_SP])) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __shared__ double sums[2];
-        if (warp < 2) {
-            double v = warp_sum_parts(part + warp * gridDim.x, gridDim.x, lane);
-            if (lane == 0) sums[warp] = v;
-        }
-        __syncthreads();
+        const double spq = block_sum_parts(part, gridDim.x, sh);
+        const double spr = block_sum_parts(part + gridDim.x, gridDim.x, sh);
         if (threadIdx.x == 0) {
-            double spq = sums[0], spr = sums[1];
-            double al = spr / spq;
+            const double al = spr / spq;
             if (!(spq > 0.0) || !isfinite(al)) {
                 flag[F_STOP] = 2;
             } else {
@@ -416,16 +424,14 @@ __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p
     v = block_sum(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
     if (last_block(&flag[F_T_XR])) {
-        if (threadIdx.x < 32) {
-            double rr = warp_sum_parts(part, RB, threadIdx.x);
-            if (threadIdx.x == 0) {
-                double rel = sqrt(rr) / scal[S_BNORM];
-                scal[S_REL] = rel;
-                flag[F_ITERS] += 1;
-                if (!isfinite(rel)) flag[F_STOP] = 2;
-                else if (rel < tol) flag[F_STOP] = 1;
-                flag[F_T_XR] = 0;
-            }
+        const double rr = block_sum_parts(part, RB, sh);
+        if (threadIdx.x == 0) {
+            const double rel = sqrt(rr) / scal[S_BNORM];
+            scal[S_REL] = rel;
+            flag[F_ITERS] += 1;
+            if (!isfinite(rel)) flag[F_STOP] = 2;
+            else if (rel < tol) flag[F_STOP] = 1;
+            flag[F_T_XR] = 0;
         }
     }
 }
@@ -536,7 +542,8 @@ struct FcgRun {
             DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
             DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
             DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
-            DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)(MAXM * RB + 2 * cdiv(nf, KT) + RB + 8)));
+            // partials: multidot (MAXM x RB), SpMV dots (2 x nb_spmv <= 2 x RB), |r|^2 (RB)
+            DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)((MAXM + 3) * RB + 8)));
             DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
             p->kr_m = m;
         }
@@ -564,7 +571,7 @@ struct FcgRun {
         L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
         ev.resize(4 * std::max(POLL, L));
         for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
-        nb_spmv = cdiv(nf, KT);
+        nb_spmv = std::min(RB, cdiv(nf, KT / LPR));
         off_sp = OFF_MD + MAXM * RB;
         off_rr = off_sp + 2LL * nb_spmv;
         use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;

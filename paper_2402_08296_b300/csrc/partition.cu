@@ -217,14 +217,17 @@ __global__ void k_mem_layer(const int *rowptr, const int *col, const int *mptr, 
     }
 }
 
-__global__ void k_pairs(const int *mptr, const int *midx, int nf, int *pnode, int *psub, int *mult) {
+__global__ void k_pairs(const int *mptr, const int *midx, int nf, int *pnode, int *psub, int *mult,
+                        double *inv_mult) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     for (int q = mptr[f]; q < mptr[f + 1]; ++q) {
         pnode[q] = f;
         psub[q] = midx[q];
     }
-    mult[f] = mptr[f + 1] - mptr[f];
+    const int m = mptr[f + 1] - mptr[f];
+    mult[f] = m;
+    inv_mult[f] = 1.0 / m;  // the partition-of-unity weight, divided once here
 }
 
 __global__ void k_sub_lists(const int *order, const int *pnode, const int *psub, int total, int *sub_idx,
@@ -661,7 +664,8 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     DDG_CU(cudaMallocAsync(&psub, sizeof(int) * total, s));
     DDG_CU(cudaMallocAsync(&order, sizeof(int) * total, s));
     DDG_TRY(dalloc(c, p->a_part, &p->mult, nf));
-    k_pairs<<<cdiv(nf, 256), 256, 0, s>>>(p->mem_ptr, p->mem_idx, nf, pnode, psub, p->mult);
+    DDG_TRY(dalloc(c, p->a_part, &p->inv_mult, nf));
+    k_pairs<<<cdiv(nf, 256), 256, 0, s>>>(p->mem_ptr, p->mem_idx, nf, pnode, psub, p->mult, p->inv_mult);
     DDG_LAUNCH_CHECK();
     DDG_TRY(sort_pairs(c, psub, pnode, total, order, s));
     DDG_TRY(dalloc(c, p->a_part, &p->sub_idx, total));
