@@ -3,6 +3,8 @@
 // of the other translation units.
 #include "ddg_internal.cuh"
 
+#include <cstdlib>
+
 #include <algorithm>
 #include <cstring>
 
@@ -73,6 +75,7 @@ int32_t ddg_create(int32_t device, size_t hbm_budget_bytes, ddg_ctx **out) {
     ddg_ctx *c = new ddg_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes;
+    c->pdl = getenv("DDG_NO_PDL") == nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;

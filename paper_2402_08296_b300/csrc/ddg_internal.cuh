@@ -74,6 +74,7 @@ struct ddg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t budget = 0;
+    bool pdl = true;  // programmatic dependent launches between GNN blocks (DDG_NO_PDL=1 turns them off)
     std::atomic<size_t> in_use{0};
     ddg::Server *server = nullptr;  // started by the first ddg_submit
     std::mutex server_mu;

@@ -871,6 +871,9 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
     float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     const float4 *hrow_in = reinterpret_cast<const float4 *>(a.h_in);  // rows of 12: h[10], c, 0
+    // launched as a programmatic dependent of the previous block: everything above reads
+    // set-up data only; wait here until the previous launch's latents are complete and visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // phase A: projections and coordinates of every needed node
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
@@ -885,7 +888,6 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
         XY[u] = a.loc_xy[node];
     }
     __syncthreads();
-    const f2_t *Pb2 = reinterpret_cast<const f2_t *>(Pb);  // per node: o01 i01 o23 i23 ...
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int u = p * T + tid;
@@ -926,9 +928,10 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
             const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn);
             f2_t po[D / 2], pi[D / 2];
 #pragma unroll
-            for (int m = 0; m < D / 2; ++m) {
-                po[m] = Pb2[(size_t)v * 10 + 2 * m];
-                pi[m] = Pb2[(size_t)v * 10 + 2 * m + 1];
+            for (int m = 0; m < D / 2; ++m) {  // one 16-byte shared load per output pair of both messages
+                const float4 t = Pb[(size_t)v * 5 + m];
+                po[m] = f2_pack(t.x, t.y);
+                pi[m] = f2_pack(t.z, t.w);
             }
             f2_msg<F_WEO, true>(so, pao, po, Wp, dx2, dy2, dn2, f2_pack(mo, mo));
             if (inner) f2_msg<F_WEI, false>(si, pai, pi, Wp, dx2, dy2, dn2, 0ull);
@@ -1002,6 +1005,9 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
             hrow_out[2] = make_float4(hn[8], hn[9], c, 0.f);
         }
     }
+    // this CTA's writes are issued: the next block's CTAs may be scheduled (they still wait
+    // for the whole grid at their griddepcontrol.wait)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Set-up of a global chunk plan, one CTA per chunk: the chunk's own nodes are the
@@ -1485,7 +1491,19 @@ static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t 
         a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
         a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
         const FusedWeights *W = reinterpret_cast<const FusedWeights *>(w_fused_host(p)) + blk;
-        k_dss_fused<T><<<p->chunk.nchunks, T, smem, s>>>(*W, a);
+        // programmatic dependent launch: block blk+1's CTAs are scheduled as block blk's CTAs
+        // retire, hiding the launch gap between the 30 launches of an application
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(p->chunk.nchunks);
+        cfg.blockDim = dim3(T);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = p->ctx->pdl ? 1 : 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DDG_CU(cudaLaunchKernelEx(&cfg, k_dss_fused<T>, *W, a));
     }
     DDG_LAUNCHES(m->kbar);
     return DDG_OK;

@@ -25,7 +25,7 @@ namespace ddg {
 
 constexpr int KT = 256;            // threads per block of the vector kernels
 constexpr int RB = 1184;           // fixed grid of the streaming kernels: 8 CTAs of 256 on each of 148 SMs
-constexpr int LPR = 8;             // lanes per CSR row in the SpMV
+constexpr int MDG = 592;           // grid of the multi-dot and the direction update (4 CTAs of 256 per SM)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
@@ -35,35 +35,56 @@ enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT
 enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
 
 // ------------------------------------------------------------------ SpMV
-// y_i = sum_e val[e] x[col[e]] with LPR lanes per row: a row's entries are read by
-// consecutive lanes (coalesced), then summed by a fixed shuffle tree.  Every lane of
-// the warp calls it (rows i >= n contribute nothing), so the full-warp shuffles are
-// always executed by all 32 lanes.  Returns the row's value in every lane of its group.
-__device__ __forceinline__ double csr_row(const int *__restrict__ rowptr, const int *__restrict__ col,
-                                          const double *__restrict__ val, const double *__restrict__ x, int i,
-                                          int n, int sub) {
-    double acc = 0.0;
-    const int e0 = i < n ? rowptr[i] + sub : 0, e1 = i < n ? rowptr[i + 1] : 0;
-    for (int e = e0; e < e1; e += LPR) acc += val[e] * x[col[e]];
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LPR);
-    return acc;
+// y_i = sum_e val[e] x[col[e]], one row per thread, a block per 256 consecutive rows.
+// The block first copies its rows' column indices and values (one contiguous range)
+// into shared memory with coalesced loads, then every thread sums its row from there
+// in CSR order (the same order, hence the same result, as a plain row loop).
+constexpr int SP_NNZ = 3072;  // shared-memory tile: up to 12 entries per row on average
+
+template <bool DOTS>
+__device__ __forceinline__ void spmv_tile(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                          const double *__restrict__ val, const double *__restrict__ x,
+                                          double *__restrict__ y, int n, const double *__restrict__ r,
+                                          double &pq, double &pr) {
+    __shared__ int scol[SP_NNZ];
+    __shared__ double sval[SP_NNZ];
+    const int r0 = blockIdx.x * KT, r1 = min(n, r0 + KT);
+    const int i = r0 + threadIdx.x;
+    const int eb = rowptr[r0], ee = rowptr[r1];
+    const bool tiled = ee - eb <= SP_NNZ;  // uniform over the block
+    if (tiled) {
+        for (int e = eb + threadIdx.x; e < ee; e += KT) {
+            scol[e - eb] = col[e];
+            sval[e - eb] = val[e];
+        }
+    }
+    __syncthreads();
+    if (i < n) {
+        const int e0 = rowptr[i], e1 = rowptr[i + 1];
+        double acc = 0.0;
+        if (tiled) {
+            for (int e = e0 - eb; e < e1 - eb; ++e) acc += sval[e] * x[scol[e]];
+        } else {
+            for (int e = e0; e < e1; ++e) acc += val[e] * x[col[e]];
+        }
+        y[i] = acc;
+        if (DOTS) {
+            const double xi = x[i];
+            pq = xi * acc;
+            pr = xi * r[i];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
                                              const double *__restrict__ val, const double *__restrict__ x,
                                              double *__restrict__ y, int n) {
-    const int sub = threadIdx.x % LPR;
-    const int rows_per_grid = gridDim.x * (KT / LPR);
-    for (int i0 = blockIdx.x * (KT / LPR); i0 < n; i0 += rows_per_grid) {  // uniform over the block
-        const int i = i0 + threadIdx.x / LPR;
-        const double acc = csr_row(rowptr, col, val, x, i, n, sub);
-        if (sub == 0 && i < n) y[i] = acc;
-    }
+    double pq = 0.0, pr = 0.0;
+    spmv_tile<false>(rowptr, col, val, x, y, n, nullptr, pq, pr);
 }
 
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
-    k_spmv<<<std::min(RB, cdiv(p->nf, KT / LPR)), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf);
+    k_spmv<<<cdiv(p->nf, KT), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf);
     DDG_LAUNCH_CHECK();
     return DDG_OK;
 }
@@ -326,7 +347,7 @@ __global__ void __launch_bounds__(KT, 4) k_multidot(const double *z, const doubl
     double acc[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
-    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) {
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
         double zi = z[i];
 #pragma unroll
         for (int j = 0; j < MAXM; ++j)
@@ -342,7 +363,7 @@ __global__ void __launch_bounds__(KT, 4) k_multidot(const double *z, const doubl
     if (last_block(&flag[F_T_MD])) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int j = warp; j < win.W; j += KT / 32) {
-            double d = warp_sum_parts(part + j * RB, RB, lane);
+            double d = warp_sum_parts(part + j * RB, gridDim.x, lane);
             if (lane == 0) scal[S_BETA + j] = d / scal[S_PQ + win.slot[j]];
         }
         if (threadIdx.x == 0) flag[F_T_MD] = 0;
@@ -365,27 +386,16 @@ __global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, l
     }
 }
 
-// q = A p with the partial dots p.q and p.r (LPR lanes per row, fixed grid of RB
-// blocks striding over the rows); the last block forms alpha = (p.r) / (p.q)
+// q = A p with the partial dots p.q and p.r (one row per thread, shared-memory tiles);
+// the last block forms alpha = (p.r) / (p.q)
 __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
                                                  const double *__restrict__ val, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
                                                  double *part, Window win, double *scal, int *flag) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
-    const int sub = threadIdx.x % LPR;
-    const int rows_per_grid = gridDim.x * (KT / LPR);
     double pq = 0.0, pr = 0.0;
-    for (int i0 = blockIdx.x * (KT / LPR); i0 < n; i0 += rows_per_grid) {  // uniform over the block
-        const int i = i0 + threadIdx.x / LPR;
-        const double acc = csr_row(rowptr, col, val, p, i, n, sub);
-        if (sub == 0 && i < n) {
-            q[i] = acc;
-            const double pi = p[i];
-            pq += pi * acc;
-            pr += pi * r[i];
-        }
-    }
+    spmv_tile<true>(rowptr, col, val, p, q, n, r, pq, pr);
     pq = block_sum(pq, sh);
     pr = block_sum(pr, sh);
     if (threadIdx.x == 0) {
@@ -542,8 +552,8 @@ struct FcgRun {
             DDG_TRY(dalloc(c, p->a_kry, &p->kP, (size_t)m * nf));
             DDG_TRY(dalloc(c, p->a_kry, &p->kQ, (size_t)m * nf));
             DDG_TRY(dalloc(c, p->a_kry, &p->kscal, S_COUNT + 8));
-            // partials: multidot (MAXM x RB), SpMV dots (2 x nb_spmv <= 2 x RB), |r|^2 (RB)
-            DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)((MAXM + 3) * RB + 8)));
+            // partials: multidot (MAXM x RB), SpMV dots (2 per row block), |r|^2 (RB)
+            DDG_TRY(dalloc(c, p->a_kry, &p->kpart, (size_t)((MAXM + 1) * RB + 2 * cdiv(nf, KT) + 8)));
             DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
             p->kr_m = m;
         }
@@ -571,7 +581,7 @@ struct FcgRun {
         L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
         ev.resize(4 * std::max(POLL, L));
         for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
-        nb_spmv = std::min(RB, cdiv(nf, KT / LPR));
+        nb_spmv = cdiv(nf, KT);
         off_sp = OFF_MD + MAXM * RB;
         off_rr = off_sp + 2LL * nb_spmv;
         use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;
@@ -598,11 +608,11 @@ struct FcgRun {
         }
         double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
         if (win.W > 0) {
-            k_multidot<<<RB, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
+            k_multidot<<<MDG, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
             launches += 1;
             DDG_LAUNCHES(1);
         }
-        k_pupdate<<<RB, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
+        k_pupdate<<<MDG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
         k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
         k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
         launches += 3;
