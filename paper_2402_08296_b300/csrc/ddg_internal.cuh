@@ -239,6 +239,14 @@ int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
 int32_t chunk_build(ddg_problem *p, int T);
 int32_t chunk_build_global(ddg_problem *p, int T);
+// fused GNN steps over several problems (request loop): schedule 3 with chunk width GROUP_T
+constexpr int GROUP_T = 128;
+struct ChunkArgs;
+int32_t dss_group_prepare(ddg_problem *p);
+bool dss_group_compatible(const ddg_problem *a, const ddg_problem *b);
+size_t dss_group_args_bytes();
+int32_t dss_group_launch(ddg_problem *const *ps, const double *const *rs, const int *const *stops, int n,
+                         ChunkArgs *dev_args, bool upload, cudaStream_t s);
 void chunk_free(ddg_problem *p);
 int32_t model_xavier(ddg_model *m, uint64_t seed);
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s);
@@ -252,6 +260,17 @@ int32_t fcg_begin(FcgRun *r, ddg_problem *p, const double *x0, double rtol, int 
 int32_t fcg_launch_batch(FcgRun *r);
 int32_t fcg_check(FcgRun *r, bool blocking, bool *ready, bool *done);
 int32_t fcg_end(FcgRun *r, double *x_host, ddg_solve_report *rep);
+// fused-step mode: group_pre (restriction, coarse solve) and group_post (gluing and the FCG
+// kernels, then the iteration counter advances) bracket a fused GNN launch over several runs;
+// group_mark queues the flag copy that fcg_check observes
+int32_t fcg_group_pre(FcgRun *r);
+int32_t fcg_group_post(FcgRun *r);
+int32_t fcg_group_mark(FcgRun *r);
+int fcg_group_since_mark(const FcgRun *r);
+int fcg_iterations_launched(const FcgRun *r);
+int fcg_max_iter(const FcgRun *r);
+const double *fcg_residual(const FcgRun *r);
+const int *fcg_flag(const FcgRun *r);
 int32_t train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts *o, ddg_train_report *rep);
 int32_t train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int *graphs_host, int nb,
                         double *loss, float *grad_host);

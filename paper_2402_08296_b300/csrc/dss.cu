@@ -855,12 +855,14 @@ __host__ __device__ __forceinline__ size_t fused_smem(int nn) {
     return (size_t)nn * (5 * sizeof(float4) + sizeof(float2));
 }
 
+// One CTA of schedule 3 on chunk q of the plan in `a`; first/last mark the first and last
+// message-passing block, h_in/h_out the latent rows read and written.
 template <int T>
-__global__ void __launch_bounds__(T, 65536 / (T * 128))
-    k_dss_fused(const __grid_constant__ FusedWeights W, const __grid_constant__ ChunkArgs a) {
+__device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkArgs &a, int q, bool first, bool last,
+                                            const float *h_in, float *h_out) {
     extern __shared__ __align__(16) float4 smem4[];
     if (a.stop && *a.stop) return;
-    const int q = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const int own = a.c_own[q];
     const int nn = a.c_need_n[q];
     const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
@@ -870,7 +872,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
     float4 *Pb = smem4;                                               // [nn][5]
     float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
-    const float4 *hrow_in = reinterpret_cast<const float4 *>(a.h_in);  // rows of 12: h[10], c, 0
+    const float4 *hrow_in = reinterpret_cast<const float4 *>(h_in);  // rows of 12: h[10], c, 0
     // launched as a programmatic dependent of the previous block: everything above reads
     // set-up data only; wait here until the previous launch's latents are complete and visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -878,7 +880,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
         float h[D], cdummy;
-        if (a.first) {
+        if (first) {
 #pragma unroll
             for (int o = 0; o < D; ++o) h[o] = 0.f;
         } else {
@@ -896,7 +898,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
         const int node = inf.x;
         const bool inner = inf.y >= 0;
         float hp[D], c;  // read again (a cache hit) rather than held across the barrier
-        if (a.first) {
+        if (first) {
 #pragma unroll
             for (int o = 0; o < D; ++o) hp[o] = 0.f;
             const double s = a.s[inf.w];
@@ -981,7 +983,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
             const f2_t hv = f2_add(f2_pack(hp[2 * m], hp[2 * m + 1]), out[m]);
             f2_unpack(hv, hn[2 * m], hn[2 * m + 1]);
         }
-        if (a.last) {
+        if (last) {
             if (inner) {
                 f2_t dh[D / 2];
 #pragma unroll
@@ -999,7 +1001,7 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
                 a.corr[inf.y] = s == 0.0 ? 0.0 : s * (double)y;
             }
         } else {
-            float4 *hrow_out = reinterpret_cast<float4 *>(a.h_out) + 3 * (size_t)node;
+            float4 *hrow_out = reinterpret_cast<float4 *>(h_out) + 3 * (size_t)node;
             hrow_out[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
             hrow_out[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
             hrow_out[2] = make_float4(hn[8], hn[9], c, 0.f);
@@ -1008,6 +1010,36 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128))
     // this CTA's writes are issued: the next block's CTAs may be scheduled (they still wait
     // for the whole grid at their griddepcontrol.wait)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 128))
+    k_dss_fused(const __grid_constant__ FusedWeights W, const __grid_constant__ ChunkArgs a) {
+    fused_chunk<T>(W, a, blockIdx.x, a.first, a.last, a.h_in, a.h_out);
+}
+
+// Several problems' graphs in one launch (the request loop's fused GNN step): CTA b runs
+// chunk b - cpre[i] of problem i, where cpre[i] <= b < cpre[i + 1].  Every problem's
+// descriptor holds its latent buffers in block-0 orientation; odd blocks swap them.
+constexpr int MAX_GROUP = 32;
+struct GroupArgs {
+    int n;                      // problems in the group
+    int first, last, odd;       // block flags
+    int cpre[MAX_GROUP + 1];    // chunk prefix sums
+    const ChunkArgs *args;      // [n] descriptors (device)
+};
+
+template <int T>
+__global__ void __launch_bounds__(T, 65536 / (T * 128))
+    k_dss_fused_group(const __grid_constant__ FusedWeights W, const __grid_constant__ GroupArgs g) {
+    int lo = 0, hi = g.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (g.cpre[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const ChunkArgs &a = g.args[lo];
+    fused_chunk<T>(W, a, blockIdx.x - g.cpre[lo], g.first != 0, g.last != 0, g.odd ? a.h_out : a.h_in,
+                   g.odd ? const_cast<float *>(a.h_in) : a.h_out);
 }
 
 // Set-up of a global chunk plan, one CTA per chunk: the chunk's own nodes are the
@@ -1509,7 +1541,7 @@ static int32_t launch_fused(ddg_problem *p, const ChunkArgs &base, cudaStream_t 
     return DDG_OK;
 }
 
-int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+static ChunkArgs chunk_args(ddg_problem *p, const double *r, const int *stop) {
     const ChunkPlan &cp = p->chunk;
     ChunkArgs a{};
     a.c_graph = cp.c_graph;
@@ -1536,6 +1568,14 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     a.n_total = p->sum_loc;
     a.alpha = p->model->alpha;
     a.stop = stop;
+    a.h_in = p->dss_h;
+    a.h_out = p->dss_h2;
+    return a;
+}
+
+int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
+    const ChunkPlan &cp = p->chunk;
+    const ChunkArgs a = chunk_args(p, r, stop);
     if (cp.global) {
         switch (cp.T) {
             case 128: return launch_fused<128>(p, a, s);
@@ -1550,6 +1590,86 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
         default: set_error("no chunk plan"); return DDG_INVALID_ARG;
     }
 }
+
+// ---------------------------------------------------------------- fused step over several problems
+template <int T>
+static int32_t launch_group(ddg_problem *const *ps, int n, const int *cpre, const ChunkArgs *dev_args,
+                            size_t smem, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss_fused_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024));
+        configured = true;
+    }
+    const ddg_model *m = ps[0]->model;
+    for (int blk = 0; blk < m->kbar; ++blk) {
+        GroupArgs g{};
+        g.n = n;
+        g.first = blk == 0;
+        g.last = blk == m->kbar - 1;
+        g.odd = blk & 1;
+        for (int i = 0; i <= n; ++i) g.cpre[i] = cpre[i];
+        g.args = dev_args;
+        const FusedWeights *W = reinterpret_cast<const FusedWeights *>(w_fused_host(ps[0])) + blk;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cpre[n]);
+        cfg.blockDim = dim3(T);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = ps[0]->ctx->pdl ? 1 : 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DDG_CU(cudaLaunchKernelEx(&cfg, k_dss_fused_group<T>, *W, g));
+    }
+    DDG_LAUNCHES(m->kbar);
+    return DDG_OK;
+}
+
+bool dss_group_compatible(const ddg_problem *a, const ddg_problem *b) {
+    return a->kind == DDG_DDM_GNN && b->kind == DDG_DDM_GNN && a->model == b->model && a->w_bf16 == b->w_bf16 &&
+           a->dss_sched == 3 && b->dss_sched == 3 && a->chunk.T == b->chunk.T;
+}
+
+int32_t dss_group_prepare(ddg_problem *p) {
+    if (p->kind != DDG_DDM_GNN) return DDG_INVALID_ARG;
+    if (p->dss_sched != 3 || p->chunk.T != GROUP_T || !p->chunk.global) {
+        DDG_TRY(chunk_build_global(p, GROUP_T));
+        p->dss_sched = 3;
+    }
+    return DDG_OK;
+}
+
+int32_t dss_group_launch(ddg_problem *const *ps, const double *const *rs, const int *const *stops, int n,
+                         ChunkArgs *dev_args, bool upload, cudaStream_t s) {
+    if (n < 1 || n > MAX_GROUP) {
+        set_error("a fused GNN step takes 1 to 32 problems");
+        return DDG_INVALID_ARG;
+    }
+    int cpre[MAX_GROUP + 1];
+    size_t smem = 0;
+    cpre[0] = 0;
+    std::vector<ChunkArgs> host(n);
+    for (int i = 0; i < n; ++i) {
+        if (!dss_group_compatible(ps[0], ps[i])) {
+            set_error("problems of one fused GNN step must share model, weights precision and chunk plan width");
+            return DDG_INVALID_ARG;
+        }
+        host[i] = chunk_args(ps[i], rs[i], stops[i]);
+        cpre[i + 1] = cpre[i] + ps[i]->chunk.nchunks;
+        smem = std::max(smem, ps[i]->chunk.max_smem);
+    }
+    if (upload)
+        DDG_CU(cudaMemcpyAsync(dev_args, host.data(), sizeof(ChunkArgs) * n, cudaMemcpyHostToDevice, s));
+    switch (ps[0]->chunk.T) {
+        case 128: return launch_group<128>(ps, n, cpre, dev_args, smem, s);
+        case 256: return launch_group<256>(ps, n, cpre, dev_args, smem, s);
+        default: set_error("no chunk plan"); return DDG_INVALID_ARG;
+    }
+}
+
+size_t dss_group_args_bytes() { return sizeof(ChunkArgs) * MAX_GROUP; }
 
 static size_t dss_smem_bytes(int nmax, int emax) {
     size_t b = 128 + 2 * (size_t)BLOCK_BYTES;

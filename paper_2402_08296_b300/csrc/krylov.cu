@@ -157,6 +157,29 @@ static cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
                                                                                 : cudaEventRecordDefault);
 }
 
+// the preconditioner in three parts: restriction (+ coarse solve), local solves, gluing
+static int32_t precond_pre(ddg_problem *p, const double *r, cudaStream_t s, const int *stop, bool prolong, int *nl) {
+    const int K = p->K;
+    k_restrict<<<K, KT, 0, s>>>(p->sub_ptr, p->sub_idx, p->inv_mult, r, p->s, p->y, stop);
+    DDG_LAUNCH_CHECK();
+    ++*nl;
+    if ((p->flags & DDG_COARSE) && prolong) {
+        k_coarse_gemv<<<cdiv(K, 8), 256, 0, s>>>(p->A0inv, p->y, p->wc, K, stop);
+        DDG_LAUNCH_CHECK();
+        ++*nl;
+    }
+    return DDG_OK;
+}
+
+static int32_t precond_post(ddg_problem *p, double *z, cudaStream_t s, const int *stop, int *nl) {
+    const bool coarse = (p->flags & DDG_COARSE) != 0;
+    k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->inv_mult, p->corr, p->wc,
+                                             p->nf, coarse ? 1 : 0, (p->flags & DDG_POU_PROLONG) ? 1 : 0, z, stop);
+    DDG_LAUNCH_CHECK();
+    ++*nl;
+    return DDG_OK;
+}
+
 // launches the preconditioner's kernels; ev_local (optional) brackets the local-solve kernel;
 // *launches (optional) is increased by the number of kernels launched
 static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStream_t s, const int *stop,
@@ -171,16 +194,7 @@ static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStre
         if (launches) *launches += nl;
         return DDG_OK;
     }
-    const int K = p->K;
-    k_restrict<<<K, KT, 0, s>>>(p->sub_ptr, p->sub_idx, p->inv_mult, r, p->s, p->y, stop);
-    DDG_LAUNCH_CHECK();
-    ++nl;
-    const bool coarse = (p->flags & DDG_COARSE) != 0;
-    if (coarse && prolong) {
-        k_coarse_gemv<<<cdiv(K, 8), 256, 0, s>>>(p->A0inv, p->y, p->wc, K, stop);
-        DDG_LAUNCH_CHECK();
-        ++nl;
-    }
+    DDG_TRY(precond_pre(p, r, s, stop, prolong, &nl));
     if (ev_local) DDG_CU(record_event(ev_local[0], s));
     if (p->kind == DDG_DDM_GNN) {
         DDG_TRY(dss_launch_args(p, r, stop, s));
@@ -189,13 +203,7 @@ static int32_t precond_core(ddg_problem *p, const double *r, double *z, cudaStre
     }
     if (ev_local) DDG_CU(record_event(ev_local[1], s));
     ++nl;
-    if (prolong) {
-        k_prolong<<<cdiv(p->nf, KT), KT, 0, s>>>(p->mem_ptr, p->mem_idx, p->inv_pos, p->inv_mult, p->corr, p->wc,
-                                                 p->nf, coarse ? 1 : 0, (p->flags & DDG_POU_PROLONG) ? 1 : 0, z,
-                                                 stop);
-        DDG_LAUNCH_CHECK();
-        ++nl;
-    }
+    if (prolong) DDG_TRY(precond_post(p, z, s, stop, &nl));
     if (launches) *launches += nl;
     return DDG_OK;
 }
@@ -592,6 +600,56 @@ struct FcgRun {
         return DDG_OK;
     }
 
+    // ---- fused-step mode (request loop): the caller runs the local GNN solves of several
+    // problems in one launch between group_pre and group_post of one iteration each
+    int32_t group_pre() {
+        int nl = 0;
+        DDG_TRY(precond_pre(p, r, s, flag, true, &nl));
+        launches += nl + 1;  // + this problem's share of the fused GNN launches, counted once per step
+        ++loc_applies;
+        return DDG_OK;
+    }
+
+    int32_t group_post() {
+        const int iter = it;
+        Window win{};
+        win.W = std::min(iter, m);
+        for (int j = 0; j < win.W; ++j) win.slot[j] = (iter - win.W + j) % m;
+        win.snew = iter % m;
+        int nl = 0;
+        DDG_TRY(precond_post(p, z, s, flag, &nl));
+        DDG_TRY(fcg_kernels(win, nl));
+        launches += nl;
+        ++it;
+        ++group_since_mark;
+        return DDG_OK;
+    }
+
+    int32_t group_mark() {  // queue the flag copy whose completion check() observes
+        DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
+        DDG_CU(cudaEventRecord(batch_done, s));
+        in_flight = 0;
+        group_since_mark = 0;
+        return DDG_OK;
+    }
+    int group_since_mark = 0;
+
+    // the four FCG kernels of one iteration after z = M^-1 r
+    int32_t fcg_kernels(const Window &win, int &nl) {
+        double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
+        if (win.W > 0) {
+            k_multidot<<<MDG, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
+            ++nl;
+            DDG_LAUNCHES(1);
+        }
+        k_pupdate<<<MDG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
+        k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
+        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
+        nl += 3;
+        DDG_LAUNCHES(3);
+        return DDG_OK;
+    }
+
     // launches one FCG iteration; q indexes the iteration's event slot
     int32_t launch_iter(int iter, int q) {
         Window win{};
@@ -606,17 +664,9 @@ struct FcgRun {
             ++loc_applies;
             loc_launches += (p->kind == DDG_DDM_GNN && p->dss_sched >= 1) ? p->model->kbar : 1;
         }
-        double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
-        if (win.W > 0) {
-            k_multidot<<<MDG, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
-            launches += 1;
-            DDG_LAUNCHES(1);
-        }
-        k_pupdate<<<MDG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
-        k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
-        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
-        launches += 3;
-        DDG_LAUNCHES(3);
+        int nl = 0;
+        DDG_TRY(fcg_kernels(win, nl));
+        launches += nl;
         if (record)
             DDG_CU(cudaMemcpyAsync(record + (size_t)(iter + 1) * nf, r, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
         return DDG_OK;
@@ -726,6 +776,15 @@ struct FcgRun {
         return rp.status;
     }
 };
+
+int32_t fcg_group_pre(FcgRun *r) { return r->group_pre(); }
+int32_t fcg_group_post(FcgRun *r) { return r->group_post(); }
+int32_t fcg_group_mark(FcgRun *r) { return r->group_mark(); }
+int fcg_group_since_mark(const FcgRun *r) { return r->group_since_mark; }
+int fcg_iterations_launched(const FcgRun *r) { return r->it; }
+int fcg_max_iter(const FcgRun *r) { return r->max_iter; }
+const double *fcg_residual(const FcgRun *r) { return r->r; }
+const int *fcg_flag(const FcgRun *r) { return r->flag; }
 
 FcgRun *fcg_new() { return new FcgRun(); }
 void fcg_delete(FcgRun *r) { delete r; }

@@ -10,9 +10,17 @@
 // concurrently on the GPU, and a request that arrives while others are running
 // starts as soon as a slot and memory are free (continuous batching).  Krylov
 // state stays on the device between batches.  ddg_poll returns DDG_PENDING
-// until the request has finished, then its report and solution.  Results are
-// bitwise the same as a stand-alone ddg_fcg_solve, since every kernel of a
-// request only touches that request's buffers and sums in a fixed order.
+// until the request has finished, then its report and solution.
+//
+// DDM-GNN requests that share a model run as one group: every step advances
+// each member by one FCG iteration, and the local GNN solves of all members run
+// as one fused launch per message-passing block over the subdomains of every
+// member (schedule 3, chunk width GROUP_T), between the members' restriction
+// and gluing kernels on their own streams.  Members join and leave the group
+// between steps.  Results are bitwise the same as a stand-alone ddg_fcg_solve
+// with the same GNN schedule, since every CTA only touches one request's
+// buffers and every sum runs in a fixed order.  DDG_SERVE_SEPARATE=1 runs every
+// request on its own instead (for comparison).
 #include "ddg_internal.cuh"
 
 #include <algorithm>
@@ -23,9 +31,12 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <cstdlib>
 #include <thread>
 
 namespace ddg {
+
+static constexpr int MAX_GROUP_REQUESTS = 32;  // problems of one fused GNN launch
 
 static double now_ms() {
     using namespace std::chrono;
@@ -42,6 +53,9 @@ struct ServeRequest {
     ddg_problem *p = nullptr;
     FcgRun *run = nullptr;
     int32_t status = DDG_PENDING;
+    bool grouped = false;       // member of the fused GNN group
+    bool marked = false;        // a flag copy is queued (fcg_check can observe it)
+    cudaEvent_t ev_pre = nullptr;
     ddg_solve_report rep{};
     std::vector<double> x;
     std::string err;
@@ -64,7 +78,20 @@ struct Server {
     std::vector<double> latencies;
     uint64_t completed = 0, failed = 0;
     double t_first_submit = -1.0, t_last_done = 0.0;
+    // fused GNN group (used by the scheduler thread only)
+    bool fuse = true;
+    std::vector<ServeRequest *> group;
+    std::vector<ddg_problem *> uploaded;  // members of the last descriptor upload
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_gnn = nullptr;
+    static constexpr int DEPTH = 4;       // group steps queued ahead of the host
+    cudaEvent_t ev_step[DEPTH] = {};
+    int steps = 0, steps_done = 0;
+    ChunkArgs *gargs = nullptr;           // device descriptors of the members
+    Allocs gallocs;
 };
+
+static constexpr int GROUP_POLL = 4;  // group steps between flag copies of a member
 
 // device memory of one request: mesh, matrix, decomposition, Krylov rings, and the
 // preconditioner (band factors for DDM-LU, latents for DDM-GNN) plus the coarse matrix
@@ -78,6 +105,19 @@ static void finish(Server *S, ServeRequest *q, int32_t status, const std::string
     q->status = status;
     q->err = err;
     q->t_done = now_ms();
+    if (q->grouped) {
+        // every queued step that holds this member ends before its stream's last gluing kernel,
+        // which fcg_end (or this synchronisation) waits for; then the member leaves the group
+        if (q->p) cudaStreamSynchronize(q->p->stream);
+        if (S->gstream) cudaStreamSynchronize(S->gstream);
+        S->uploaded.clear();
+        S->group.erase(std::remove(S->group.begin(), S->group.end(), q), S->group.end());
+        q->grouped = false;
+    }
+    if (q->ev_pre) {
+        cudaEventDestroy(q->ev_pre);
+        q->ev_pre = nullptr;
+    }
     if (q->run) {
         fcg_delete(q->run);
         q->run = nullptr;
@@ -119,10 +159,58 @@ static int32_t start(Server *S, ServeRequest *q) {
     K = std::min(K, q->p->nf);
     DDG_TRY(ddg_partition(q->p, K, q->opts.overlap, nullptr));
     DDG_TRY(ddg_setup_precond(q->p, q->opts.kind, q->opts.model, q->opts.flags));
+    q->x.resize(n);
+    bool join = S->fuse && q->opts.kind == DDG_DDM_GNN && (int)S->group.size() < MAX_GROUP_REQUESTS;
+    if (join) {
+        DDG_TRY(dss_group_prepare(q->p));
+        join = S->group.empty() || dss_group_compatible(S->group[0]->p, q->p);
+    }
     q->run = fcg_new();
     DDG_TRY(fcg_begin(q->run, q->p, nullptr, q->opts.rtol, q->opts.max_iter, q->opts.m_trunc));
-    q->x.resize(n);
+    if (join) {
+        DDG_CU(cudaEventCreateWithFlags(&q->ev_pre, cudaEventDisableTiming));
+        q->grouped = true;
+        S->group.push_back(q);
+        return DDG_OK;
+    }
     return fcg_launch_batch(q->run);
+}
+
+// one fused step: every member that still has iterations to run advances by one
+static int32_t group_step(Server *S, bool *launched) {
+    std::vector<ServeRequest *> mem;
+    for (ServeRequest *q : S->group)
+        if (fcg_iterations_launched(q->run) < fcg_max_iter(q->run)) mem.push_back(q);
+    *launched = false;
+    if (mem.empty()) return DDG_OK;
+    std::vector<ddg_problem *> ps;
+    std::vector<const double *> rs;
+    std::vector<const int *> stops;
+    for (ServeRequest *q : mem) {
+        DDG_TRY(fcg_group_pre(q->run));
+        DDG_CU(cudaEventRecord(q->ev_pre, q->p->stream));
+        DDG_CU(cudaStreamWaitEvent(S->gstream, q->ev_pre, 0));
+        ps.push_back(q->p);
+        rs.push_back(fcg_residual(q->run));
+        stops.push_back(fcg_flag(q->run));
+    }
+    const bool upload = ps != S->uploaded;
+    DDG_TRY(dss_group_launch(ps.data(), rs.data(), stops.data(), (int)ps.size(), S->gargs, upload, S->gstream));
+    S->uploaded = ps;
+    DDG_CU(cudaEventRecord(S->ev_gnn, S->gstream));
+    for (ServeRequest *q : mem) {
+        DDG_CU(cudaStreamWaitEvent(q->p->stream, S->ev_gnn, 0));
+        DDG_TRY(fcg_group_post(q->run));
+        if (!q->marked && (fcg_group_since_mark(q->run) >= GROUP_POLL ||
+                           fcg_iterations_launched(q->run) >= fcg_max_iter(q->run))) {
+            DDG_TRY(fcg_group_mark(q->run));
+            q->marked = true;
+        }
+    }
+    DDG_CU(cudaEventRecord(S->ev_step[S->steps % Server::DEPTH], S->gstream));
+    ++S->steps;
+    *launched = true;
+    return DDG_OK;
 }
 
 static void loop(Server *S) {
@@ -152,8 +240,9 @@ static void loop(Server *S) {
             int32_t s = start(S, q);
             if (s != DDG_OK) finish(S, q, s, last_error_cstr());
         }
-        for (ServeRequest *q : act) {
-            if (!q->run || std::find(admit.begin(), admit.end(), q) != admit.end()) continue;
+        for (ServeRequest *q : act) {  // requests on their own (group members are handled below)
+            // (admitted this round: started above, possibly already finished and collected)
+            if (std::find(admit.begin(), admit.end(), q) != admit.end() || !q->run || q->grouped) continue;
             bool ready = false, done = false;
             int32_t s = fcg_check(q->run, false, &ready, &done);
             if (s != DDG_OK) {
@@ -170,6 +259,42 @@ static void loop(Server *S) {
             } else {
                 s = fcg_launch_batch(q->run);
                 if (s != DDG_OK) finish(S, q, s, last_error_cstr());
+            }
+        }
+        // fused GNN group: queue steps while fewer than DEPTH are in flight
+        while (!S->group.empty()) {
+            while (S->steps_done < S->steps &&
+                   cudaEventQuery(S->ev_step[S->steps_done % Server::DEPTH]) == cudaSuccess)
+                ++S->steps_done;
+            cudaGetLastError();
+            if (S->steps - S->steps_done >= Server::DEPTH) break;
+            bool launched = false;
+            int32_t s = group_step(S, &launched);
+            if (s != DDG_OK) {  // a launch failed: fail every member
+                std::vector<ServeRequest *> g = S->group;
+                for (ServeRequest *q : g) finish(S, q, s, last_error_cstr());
+                progressed = true;
+                break;
+            }
+            if (!launched) break;
+            progressed = true;
+        }
+        for (ServeRequest *q : std::vector<ServeRequest *>(S->group)) {
+            if (!q->marked) continue;
+            bool ready = false, done = false;
+            int32_t s = fcg_check(q->run, false, &ready, &done);
+            if (s != DDG_OK) {
+                finish(S, q, s, last_error_cstr());
+                progressed = true;
+                continue;
+            }
+            if (!ready) continue;
+            q->marked = false;
+            progressed = true;
+            if (done) {
+                int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
+                q->rep.solve_ms = now_ms() - q->t_admit;
+                finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
             }
         }
         if (!progressed) {
@@ -189,6 +314,12 @@ void server_stop(ddg_ctx *c) {
     }
     if (S->th.joinable()) S->th.join();
     for (auto &kv : S->finished) delete kv.second;
+    if (S->gstream) cudaStreamSynchronize(S->gstream);
+    dfree_all(c, S->gallocs);
+    for (int k = 0; k < Server::DEPTH; ++k)
+        if (S->ev_step[k]) cudaEventDestroy(S->ev_step[k]);
+    if (S->ev_gnn) cudaEventDestroy(S->ev_gnn);
+    if (S->gstream) cudaStreamDestroy(S->gstream);
     delete S;
     c->server = nullptr;
 }
@@ -198,6 +329,14 @@ static Server *server_get(ddg_ctx *c) {
     if (!c->server) {
         Server *S = new Server();
         S->ctx = c;
+        S->fuse = getenv("DDG_SERVE_SEPARATE") == nullptr;
+        cudaSetDevice(c->device);
+        bool ok = cudaStreamCreateWithFlags(&S->gstream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&S->ev_gnn, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < Server::DEPTH && ok; ++k)
+            ok = cudaEventCreateWithFlags(&S->ev_step[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && dalloc(c, S->gallocs, reinterpret_cast<char **>(&S->gargs), dss_group_args_bytes()) == DDG_OK;
+        if (!ok) S->fuse = false;  // fall back to separate requests, still on the GPU
         c->server = S;
         S->th = std::thread(loop, S);
     }

@@ -25,14 +25,24 @@ def _wait(ddg, ctx, tickets, sizes, timeout=300.0):
     return out
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("mode", ["fused", "separate"])
+def test_results_alone_equal_results_in_the_mix(mode, monkeypatch):
+    """fused: the DDM-GNN requests share one GNN launch per block (schedule 3, chunk width 128);
+    separate: every request runs its own kernels on its own stream."""
     import paper_2402_08296_b300 as ddg
+    # the stand-alone solves use the schedule the request loop's fused steps use
+    monkeypatch.setenv("DDG_GNN_SCHEDULE", "3")
+    monkeypatch.setenv("DDG_GNN_CHUNK_T", "128")
+    if mode == "separate":
+        monkeypatch.setenv("DDG_SERVE_SEPARATE", "1")
+    else:
+        monkeypatch.delenv("DDG_SERVE_SEPARATE", raising=False)
     ctx = ddg.ddg_create(0)
     W = synth.dss_weights(30, 10, 21, bias_scale=0.05)
     m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
     try:
         reqs = []
-        for i, n in enumerate([6000, 20000, 9000, 40000, 12000, 5000]):
+        for i, n in enumerate([6000, 20000, 9000, 40000, 12000, 5000, 15000, 7000]):
             mesh = synth.star_mesh(n, seed=300 + i)
             kind = ddg.DDG_DDM_GNN if i % 2 == 0 else ddg.DDG_DDM_LU
             reqs.append((mesh, synth.poly_coeffs(300 + i), kind))
@@ -48,7 +58,7 @@ def test_results_alone_equal_results_in_the_mix():
             alone.append((rep, x))
             ddg.ddg_problem_destroy(p)
         # in the mix: all submitted at once, solved concurrently by the scheduler
-        ddg.ddg_serve_config(ctx, 4)
+        ddg.ddg_serve_config(ctx, 6)
         tickets = [ddg.ddg_submit(ctx, mesh.xy, mesh.tri, r, kind, m if kind == ddg.DDG_DDM_GNN else None,
                                   max_iter=600) for mesh, r, kind in reqs]
         res = _wait(ddg, ctx, tickets, [mesh.n for mesh, _, _ in reqs])
