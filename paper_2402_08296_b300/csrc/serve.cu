@@ -78,17 +78,27 @@ struct Server {
     std::vector<double> latencies;
     uint64_t completed = 0, failed = 0;
     double t_first_submit = -1.0, t_last_done = 0.0;
-    // fused GNN group (used by the scheduler thread only)
+    // fused GNN groups (used by the scheduler thread only): two, stepped alternately, so that
+    // one group's GNN launches overlap the other group's Krylov kernels
     bool fuse = true;
-    std::vector<ServeRequest *> group;
-    std::vector<ddg_problem *> uploaded;  // members of the last descriptor upload
-    cudaStream_t gstream = nullptr;
-    cudaEvent_t ev_gnn = nullptr;
-    static constexpr int DEPTH = 4;       // group steps queued ahead of the host
-    cudaEvent_t ev_step[DEPTH] = {};
-    int steps = 0, steps_done = 0;
-    ChunkArgs *gargs = nullptr;           // device descriptors of the members
+    struct Group {
+        std::vector<ServeRequest *> members;
+        std::vector<ddg_problem *> uploaded;  // members of the last descriptor upload
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev_gnn = nullptr;
+        static constexpr int DEPTH = 4;       // steps queued ahead of the host
+        cudaEvent_t ev_step[DEPTH] = {};
+        int steps = 0, steps_done = 0;
+        ChunkArgs *args = nullptr;            // device descriptors of the members
+    };
+    static constexpr int NGROUPS = 2;
+    Group groups[NGROUPS];
     Allocs gallocs;
+    size_t grouped() const {
+        size_t n = 0;
+        for (const Group &g : groups) n += g.members.size();
+        return n;
+    }
 };
 
 static constexpr int GROUP_POLL = 4;  // group steps between flag copies of a member
@@ -106,12 +116,15 @@ static void finish(Server *S, ServeRequest *q, int32_t status, const std::string
     q->err = err;
     q->t_done = now_ms();
     if (q->grouped) {
-        // every queued step that holds this member ends before its stream's last gluing kernel,
-        // which fcg_end (or this synchronisation) waits for; then the member leaves the group
-        if (q->p) cudaStreamSynchronize(q->p->stream);
-        if (S->gstream) cudaStreamSynchronize(S->gstream);
-        S->uploaded.clear();
-        S->group.erase(std::remove(S->group.begin(), S->group.end(), q), S->group.end());
+        // every queued step that holds this member has ended once its stream and its group's
+        // stream are idle; then the member leaves the group
+        for (Server::Group &g : S->groups) {
+            if (std::find(g.members.begin(), g.members.end(), q) == g.members.end()) continue;
+            if (q->p) cudaStreamSynchronize(q->p->stream);
+            if (g.stream) cudaStreamSynchronize(g.stream);
+            g.uploaded.clear();
+            g.members.erase(std::remove(g.members.begin(), g.members.end(), q), g.members.end());
+        }
         q->grouped = false;
     }
     if (q->ev_pre) {
@@ -160,26 +173,37 @@ static int32_t start(Server *S, ServeRequest *q) {
     DDG_TRY(ddg_partition(q->p, K, q->opts.overlap, nullptr));
     DDG_TRY(ddg_setup_precond(q->p, q->opts.kind, q->opts.model, q->opts.flags));
     q->x.resize(n);
-    bool join = S->fuse && q->opts.kind == DDG_DDM_GNN && (int)S->group.size() < MAX_GROUP_REQUESTS;
-    if (join) {
+    // the smaller group (fewer graph nodes) takes the request, if compatible
+    Server::Group *join = nullptr;
+    if (S->fuse && q->opts.kind == DDG_DDM_GNN) {
         DDG_TRY(dss_group_prepare(q->p));
-        join = S->group.empty() || dss_group_compatible(S->group[0]->p, q->p);
+        long long best = -1;
+        for (Server::Group &g : S->groups) {
+            if ((int)g.members.size() >= MAX_GROUP_REQUESTS) continue;
+            if (!g.members.empty() && !dss_group_compatible(g.members[0]->p, q->p)) continue;
+            long long load = 0;
+            for (ServeRequest *m : g.members) load += m->p->sum_loc;
+            if (best < 0 || load < best) {
+                best = load;
+                join = &g;
+            }
+        }
     }
     q->run = fcg_new();
     DDG_TRY(fcg_begin(q->run, q->p, nullptr, q->opts.rtol, q->opts.max_iter, q->opts.m_trunc));
     if (join) {
         DDG_CU(cudaEventCreateWithFlags(&q->ev_pre, cudaEventDisableTiming));
         q->grouped = true;
-        S->group.push_back(q);
+        join->members.push_back(q);
         return DDG_OK;
     }
     return fcg_launch_batch(q->run);
 }
 
-// one fused step: every member that still has iterations to run advances by one
-static int32_t group_step(Server *S, bool *launched) {
+// one fused step of group G: every member that still has iterations to run advances by one
+static int32_t group_step(Server::Group &G, bool *launched) {
     std::vector<ServeRequest *> mem;
-    for (ServeRequest *q : S->group)
+    for (ServeRequest *q : G.members)
         if (fcg_iterations_launched(q->run) < fcg_max_iter(q->run)) mem.push_back(q);
     *launched = false;
     if (mem.empty()) return DDG_OK;
@@ -189,17 +213,17 @@ static int32_t group_step(Server *S, bool *launched) {
     for (ServeRequest *q : mem) {
         DDG_TRY(fcg_group_pre(q->run));
         DDG_CU(cudaEventRecord(q->ev_pre, q->p->stream));
-        DDG_CU(cudaStreamWaitEvent(S->gstream, q->ev_pre, 0));
+        DDG_CU(cudaStreamWaitEvent(G.stream, q->ev_pre, 0));
         ps.push_back(q->p);
         rs.push_back(fcg_residual(q->run));
         stops.push_back(fcg_flag(q->run));
     }
-    const bool upload = ps != S->uploaded;
-    DDG_TRY(dss_group_launch(ps.data(), rs.data(), stops.data(), (int)ps.size(), S->gargs, upload, S->gstream));
-    S->uploaded = ps;
-    DDG_CU(cudaEventRecord(S->ev_gnn, S->gstream));
+    const bool upload = ps != G.uploaded;
+    DDG_TRY(dss_group_launch(ps.data(), rs.data(), stops.data(), (int)ps.size(), G.args, upload, G.stream));
+    G.uploaded = ps;
+    DDG_CU(cudaEventRecord(G.ev_gnn, G.stream));
     for (ServeRequest *q : mem) {
-        DDG_CU(cudaStreamWaitEvent(q->p->stream, S->ev_gnn, 0));
+        DDG_CU(cudaStreamWaitEvent(q->p->stream, G.ev_gnn, 0));
         DDG_TRY(fcg_group_post(q->run));
         if (!q->marked && (fcg_group_since_mark(q->run) >= GROUP_POLL ||
                            fcg_iterations_launched(q->run) >= fcg_max_iter(q->run))) {
@@ -207,8 +231,8 @@ static int32_t group_step(Server *S, bool *launched) {
             q->marked = true;
         }
     }
-    DDG_CU(cudaEventRecord(S->ev_step[S->steps % Server::DEPTH], S->gstream));
-    ++S->steps;
+    DDG_CU(cudaEventRecord(G.ev_step[G.steps % Server::Group::DEPTH], G.stream));
+    ++G.steps;
     *launched = true;
     return DDG_OK;
 }
@@ -261,40 +285,45 @@ static void loop(Server *S) {
                 if (s != DDG_OK) finish(S, q, s, last_error_cstr());
             }
         }
-        // fused GNN group: queue steps while fewer than DEPTH are in flight
-        while (!S->group.empty()) {
-            while (S->steps_done < S->steps &&
-                   cudaEventQuery(S->ev_step[S->steps_done % Server::DEPTH]) == cudaSuccess)
-                ++S->steps_done;
-            cudaGetLastError();
-            if (S->steps - S->steps_done >= Server::DEPTH) break;
-            bool launched = false;
-            int32_t s = group_step(S, &launched);
-            if (s != DDG_OK) {  // a launch failed: fail every member
-                std::vector<ServeRequest *> g = S->group;
-                for (ServeRequest *q : g) finish(S, q, s, last_error_cstr());
-                progressed = true;
-                break;
+        // fused GNN groups: alternately queue one step of each while fewer than DEPTH are in flight
+        for (bool any = true; any;) {
+            any = false;
+            for (Server::Group &G : S->groups) {
+                if (G.members.empty()) continue;
+                while (G.steps_done < G.steps &&
+                       cudaEventQuery(G.ev_step[G.steps_done % Server::Group::DEPTH]) == cudaSuccess)
+                    ++G.steps_done;
+                cudaGetLastError();
+                if (G.steps - G.steps_done >= Server::Group::DEPTH) continue;
+                bool launched = false;
+                int32_t s = group_step(G, &launched);
+                if (s != DDG_OK) {  // a launch failed: fail every member
+                    std::vector<ServeRequest *> g = G.members;
+                    for (ServeRequest *q : g) finish(S, q, s, last_error_cstr());
+                    progressed = true;
+                    continue;
+                }
+                if (launched) any = progressed = true;
             }
-            if (!launched) break;
-            progressed = true;
         }
-        for (ServeRequest *q : std::vector<ServeRequest *>(S->group)) {
-            if (!q->marked) continue;
-            bool ready = false, done = false;
-            int32_t s = fcg_check(q->run, false, &ready, &done);
-            if (s != DDG_OK) {
-                finish(S, q, s, last_error_cstr());
+        for (Server::Group &G : S->groups) {
+            for (ServeRequest *q : std::vector<ServeRequest *>(G.members)) {
+                if (!q->marked) continue;
+                bool ready = false, done = false;
+                int32_t s = fcg_check(q->run, false, &ready, &done);
+                if (s != DDG_OK) {
+                    finish(S, q, s, last_error_cstr());
+                    progressed = true;
+                    continue;
+                }
+                if (!ready) continue;
+                q->marked = false;
                 progressed = true;
-                continue;
-            }
-            if (!ready) continue;
-            q->marked = false;
-            progressed = true;
-            if (done) {
-                int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
-                q->rep.solve_ms = now_ms() - q->t_admit;
-                finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
+                if (done) {
+                    int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
+                    q->rep.solve_ms = now_ms() - q->t_admit;
+                    finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
+                }
             }
         }
         if (!progressed) {
@@ -314,12 +343,14 @@ void server_stop(ddg_ctx *c) {
     }
     if (S->th.joinable()) S->th.join();
     for (auto &kv : S->finished) delete kv.second;
-    if (S->gstream) cudaStreamSynchronize(S->gstream);
+    for (Server::Group &g : S->groups) {
+        if (g.stream) cudaStreamSynchronize(g.stream);
+        for (int k = 0; k < Server::Group::DEPTH; ++k)
+            if (g.ev_step[k]) cudaEventDestroy(g.ev_step[k]);
+        if (g.ev_gnn) cudaEventDestroy(g.ev_gnn);
+        if (g.stream) cudaStreamDestroy(g.stream);
+    }
     dfree_all(c, S->gallocs);
-    for (int k = 0; k < Server::DEPTH; ++k)
-        if (S->ev_step[k]) cudaEventDestroy(S->ev_step[k]);
-    if (S->ev_gnn) cudaEventDestroy(S->ev_gnn);
-    if (S->gstream) cudaStreamDestroy(S->gstream);
     delete S;
     c->server = nullptr;
 }
@@ -331,11 +362,14 @@ static Server *server_get(ddg_ctx *c) {
         S->ctx = c;
         S->fuse = getenv("DDG_SERVE_SEPARATE") == nullptr;
         cudaSetDevice(c->device);
-        bool ok = cudaStreamCreateWithFlags(&S->gstream, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&S->ev_gnn, cudaEventDisableTiming) == cudaSuccess;
-        for (int k = 0; k < Server::DEPTH && ok; ++k)
-            ok = cudaEventCreateWithFlags(&S->ev_step[k], cudaEventDisableTiming) == cudaSuccess;
-        ok = ok && dalloc(c, S->gallocs, reinterpret_cast<char **>(&S->gargs), dss_group_args_bytes()) == DDG_OK;
+        bool ok = true;
+        for (Server::Group &g : S->groups) {
+            ok = ok && cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&g.ev_gnn, cudaEventDisableTiming) == cudaSuccess;
+            for (int k = 0; k < Server::Group::DEPTH && ok; ++k)
+                ok = cudaEventCreateWithFlags(&g.ev_step[k], cudaEventDisableTiming) == cudaSuccess;
+            ok = ok && dalloc(c, S->gallocs, reinterpret_cast<char **>(&g.args), dss_group_args_bytes()) == DDG_OK;
+        }
         if (!ok) S->fuse = false;  // fall back to separate requests, still on the GPU
         c->server = S;
         S->th = std::thread(loop, S);
