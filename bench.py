@@ -368,16 +368,12 @@ def run_serve(a, rank, local_rank):
     W, wkind = load_weights(synth)
     budget = int(a.budget_gb * (1 << 30))
 
-    def serve(kind, separate=False):
-        # fused: DDM-GNN requests share one GNN launch per block; separate: each request alone
-        if separate:
-            os.environ["DDG_SERVE_SEPARATE"] = "1"
-        else:
-            os.environ.pop("DDG_SERVE_SEPARATE", None)
+    def serve(kind, fused=False):
+        # fused: DDM-GNN requests share one GNN launch per block; otherwise each request alone
         ctx = ddg.ddg_create(local_rank, budget)
         model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, W) if kind == ddg.DDG_DDM_GNN else None
         try:
-            ddg.ddg_serve_config(ctx, a.max_active)
+            ddg.ddg_serve_config(ctx, a.max_active, fuse_gnn=fused)
             # warm-up: one small request (context, kernels, schedule tuning of the small class)
             wm = synth.star_mesh(a.n_min, seed=a.seed + 99991)
             t = ddg.ddg_submit(ctx, wm.xy, wm.tri, synth.poly_coeffs(a.seed + 99991), kind, model,
@@ -423,9 +419,8 @@ def run_serve(a, rank, local_rank):
                 "nodes": [n for _, n in tickets], "launches": launches, "clocks": clk}
 
     g = serve(ddg.DDG_DDM_GNN)
-    g_sep = serve(ddg.DDG_DDM_GNN, separate=True)
+    g_fused = serve(ddg.DDG_DDM_GNN, fused=True)
     lu = serve(ddg.DDG_DDM_LU)
-    os.environ.pop("DDG_SERVE_SEPARATE", None)
     h2d = sum(m.xy.nbytes + m.tri.nbytes + 72 for m in meshes)
     d2h = sum(8 * m.n for m in meshes)
     return {"metric": METRIC, "value": g["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
@@ -436,7 +431,7 @@ def run_serve(a, rank, local_rank):
                        "n_min": a.n_min, "n_max": a.n_max, "budget_gb": a.budget_gb, "max_active": a.max_active,
                        "kbar": KBAR, "d": D, "tol": a.tol, "fcg_m": a.m, "weights": wkind,
                        "l2": "inputs of the stream exceed L2", "parallelism": "replicas x1"},
-            "gnn": g, "gnn_separate_launches": g_sep, "lu": lu,
+            "gnn": g, "gnn_fused_launches": g_fused, "lu": lu,
             "e2e": {"value": g["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d // a.requests,
                     "d2h_bytes_per_step": d2h // a.requests,
                     "note": "the serving path is end to end: host mesh in, host solution out"},

@@ -298,8 +298,14 @@ int32_t ddg_submit(ddg_ctx *ctx, int32_t n_nodes, const double *xy, int32_t n_tr
  * report (solve_ms = wall time from admission to the result) and, if x_host
  * is not NULL, the nodal solution (n_nodes).  A ticket is collected once. */
 int32_t ddg_poll(ddg_ctx *ctx, uint64_t ticket, ddg_solve_report *report, double *x_host);
-/* Most requests in flight at once (default 64). */
-int32_t ddg_serve_config(ddg_ctx *ctx, int32_t max_active);
+/* Most requests in flight at once (default 64), and whether concurrent DDM-GNN
+ * requests share fused GNN launches (fuse_gnn = 1: each step advances every
+ * member of a group by one FCG iteration, the members' subdomains in one launch
+ * per message-passing block; 0, the default: every request runs its own
+ * kernels on its own stream, its FCG periods replayed as CUDA graphs, and the
+ * GPU overlaps the requests).  Results are the same either way.  Both settings
+ * apply to requests started after the call. */
+int32_t ddg_serve_config(ddg_ctx *ctx, int32_t max_active, int32_t fuse_gnn);
 int32_t ddg_serve_stats(ddg_ctx *ctx, ddg_serve_summary *out);
 
 #ifdef __cplusplus

@@ -12,18 +12,20 @@
 // state stays on the device between batches.  ddg_poll returns DDG_PENDING
 // until the request has finished, then its report and solution.
 //
-// DDM-GNN requests that share a model run as one group: every step advances
+// With fused GNN launches, DDM-GNN requests that share a model run in groups: every step advances
 // each member by one FCG iteration, and the local GNN solves of all members run
 // as one fused launch per message-passing block over the subdomains of every
 // member (schedule 3, chunk width GROUP_T), between the members' restriction
 // and gluing kernels on their own streams.  Members join and leave the group
 // between steps.  Results are bitwise the same as a stand-alone ddg_fcg_solve
 // with the same GNN schedule, since every CTA only touches one request's
-// buffers and every sum runs in a fixed order.  DDG_SERVE_SEPARATE=1 runs every
-// request on its own instead (for comparison).
+// buffers and every sum runs in a fixed order.  This mode is chosen with
+// ddg_serve_config; by default every request runs on its own stream with its
+// FCG periods replayed as CUDA graphs, which measured faster on one B300.
 #include "ddg_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -80,7 +82,8 @@ struct Server {
     double t_first_submit = -1.0, t_last_done = 0.0;
     // fused GNN groups (used by the scheduler thread only): two, stepped alternately, so that
     // one group's GNN launches overlap the other group's Krylov kernels
-    bool fuse = true;
+    std::atomic<bool> fuse{false};  // DDM-GNN requests join fused groups (ddg_serve_config)
+    bool fuse_ready = false;  // the groups' streams, events and descriptor buffers exist
     struct Group {
         std::vector<ServeRequest *> members;
         std::vector<ddg_problem *> uploaded;  // members of the last descriptor upload
@@ -360,7 +363,6 @@ static Server *server_get(ddg_ctx *c) {
     if (!c->server) {
         Server *S = new Server();
         S->ctx = c;
-        S->fuse = getenv("DDG_SERVE_SEPARATE") == nullptr;
         cudaSetDevice(c->device);
         bool ok = true;
         for (Server::Group &g : S->groups) {
@@ -370,7 +372,7 @@ static Server *server_get(ddg_ctx *c) {
                 ok = cudaEventCreateWithFlags(&g.ev_step[k], cudaEventDisableTiming) == cudaSuccess;
             ok = ok && dalloc(c, S->gallocs, reinterpret_cast<char **>(&g.args), dss_group_args_bytes()) == DDG_OK;
         }
-        if (!ok) S->fuse = false;  // fall back to separate requests, still on the GPU
+        S->fuse_ready = ok;  // without them every request runs on its own (still on the GPU)
         c->server = S;
         S->th = std::thread(loop, S);
     }
@@ -383,15 +385,17 @@ using namespace ddg;
 
 extern "C" {
 
-int32_t ddg_serve_config(ddg_ctx *c, int32_t max_active) {
+int32_t ddg_serve_config(ddg_ctx *c, int32_t max_active, int32_t fuse_gnn) {
     clear_error();
-    if (!c || max_active < 1) {
+    if (!c || max_active < 1 || (fuse_gnn != 0 && fuse_gnn != 1)) {
         set_error("ddg_serve_config: bad arguments");
         return DDG_INVALID_ARG;
     }
     Server *S = server_get(c);
     std::lock_guard<std::mutex> lock(S->mu);
     S->max_active = max_active;
+    // the scheduler reads `fuse` when it starts a request: switching only affects later ones
+    S->fuse = fuse_gnn != 0 && S->fuse_ready;
     return DDG_OK;
 }
 

@@ -33,10 +33,6 @@ def test_results_alone_equal_results_in_the_mix(mode, monkeypatch):
     # the stand-alone solves use the schedule the request loop's fused steps use
     monkeypatch.setenv("DDG_GNN_SCHEDULE", "3")
     monkeypatch.setenv("DDG_GNN_CHUNK_T", "128")
-    if mode == "separate":
-        monkeypatch.setenv("DDG_SERVE_SEPARATE", "1")
-    else:
-        monkeypatch.delenv("DDG_SERVE_SEPARATE", raising=False)
     ctx = ddg.ddg_create(0)
     W = synth.dss_weights(30, 10, 21, bias_scale=0.05)
     m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
@@ -58,7 +54,7 @@ def test_results_alone_equal_results_in_the_mix(mode, monkeypatch):
             alone.append((rep, x))
             ddg.ddg_problem_destroy(p)
         # in the mix: all submitted at once, solved concurrently by the scheduler
-        ddg.ddg_serve_config(ctx, 6)
+        ddg.ddg_serve_config(ctx, 6, fuse_gnn=(mode == "fused"))
         tickets = [ddg.ddg_submit(ctx, mesh.xy, mesh.tri, r, kind, m if kind == ddg.DDG_DDM_GNN else None,
                                   max_iter=600) for mesh, r, kind in reqs]
         res = _wait(ddg, ctx, tickets, [mesh.n for mesh, _, _ in reqs])
