@@ -39,6 +39,11 @@ METRIC = "Poisson solves/s to rel.res 1e-6, GNN vs LU-Schwarz on 1 B300; p50/p99
 KBAR, D, ALPHA = 30, 10, 1e-3
 WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
 L2_FLUSH_BYTES = 512 << 20
+GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused"}
+# DRAM bytes (read + write) of one GNN launch in the warm ncu capture summarised in
+# profiles/k_dss_fused_star100k.md (6.7 KB: the working set stays in L2 between the launches
+# of an application), times the 30 launches of an application; only for that workload and schedule
+GNN_TRAFFIC = {("star100k", 3): 6656 * KBAR}
 
 
 def args_parse():
@@ -273,9 +278,12 @@ def run_ours(a, rank, world, local_rank):
                 "d2h_bytes_per_step": int(w.mesh.n * 8 + 64), "wall_s": wall_e2e,
                 "p50_ms": float(np.percentile(t_e2e, 50)), "p99_ms": float(np.percentile(t_e2e, 99))},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_dss (batched DSS inference)", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": GNN_KERNELS.get(r_gnn[0]["gnn_schedule"], "k_dss") + " (batched DSS inference)",
+                     "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / fp32_peak) if achieved else None,
+                     "traffic": GNN_TRAFFIC.get((a.workload, r_gnn[0]["gnn_schedule"])),
+                     "traffic_unit": "bytes per application (ncu capture, warm L2)",
                      "flops_per_application": flops, "nodes": nodes, "messages": msgs,
                      "avg_application_ms": avg_launch_s * 1e3,
                      "gnn_schedule": r_gnn[0]["gnn_schedule"], "gnn_chunk_t": r_gnn[0]["gnn_chunk_t"],

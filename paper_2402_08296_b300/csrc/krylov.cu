@@ -324,16 +324,32 @@ __device__ __forceinline__ bool last_block(int *ticket) {
     return is_last;
 }
 
-// sum of part[0..n) by the whole block in a fixed order (valid in thread 0)
-__device__ __forceinline__ double block_sum_parts(const double *part, int n, double *sh) {
+// sum of part[0..n) by the whole block in a fixed order (valid in thread 0); the loop is
+// unrolled so that a thread's loads are in flight together (the additions keep their order)
+__device__ __forceinline__ double block_sum_parts(const double *__restrict__ part, int n, double *sh) {
     double v = 0.0;
+#pragma unroll 8
     for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
     return block_sum(v, sh);
 }
 
+// the same for two interleaved sums of part[0..n) and part[n..2n)
+__device__ __forceinline__ void block_sum_parts2(const double *__restrict__ part, int n, double *sh, double &s0,
+                                                 double &s1) {
+    double v0 = 0.0, v1 = 0.0;
+#pragma unroll 8
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        v0 += part[b];
+        v1 += part[n + b];
+    }
+    s0 = block_sum(v0, sh);
+    s1 = block_sum(v1, sh);
+}
+
 // sum of part[0..n) by one warp in a fixed order (valid in every lane)
-__device__ __forceinline__ double warp_sum_parts(const double *part, int n, int lane) {
+__device__ __forceinline__ double warp_sum_parts(const double *__restrict__ part, int n, int lane) {
     double v = 0.0;
+#pragma unroll 8
     for (int b = lane; b < n; b += 32) v += part[b];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -411,8 +427,8 @@ __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr,
         part[gridDim.x + blockIdx.x] = pr;
     }
     if (last_block(&flag[F_T_SP])) {
-        const double spq = block_sum_parts(part, gridDim.x, sh);
-        const double spr = block_sum_parts(part + gridDim.x, gridDim.x, sh);
+        double spq, spr;
+        block_sum_parts2(part, gridDim.x, sh, spq, spr);
         if (threadIdx.x == 0) {
             const double al = spr / spq;
             if (!(spq > 0.0) || !isfinite(al)) {
