@@ -10,7 +10,9 @@ learning rate drops x0.1 when the mean loss of a round over all meshes stops
 improving.
 
 Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15 [--kbar 30]
-Writes dss_k{kbar}_d10.npy (flat float32 weights, layout of include/ddg.h).
+    [--init weights.npy --lr 1e-3]
+Writes dss_k{kbar}_d10.npy (flat float32 weights, layout of include/ddg.h): of the weights after
+every round, those with which DDM-GNN FCG needs the fewest iterations on a held-out domain.
 """
 from __future__ import annotations
 
@@ -39,6 +41,10 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--harvest", type=int, default=60)
     ap.add_argument("--kbar", type=int, default=30, help="message-passing blocks (Section III-B)")
+    ap.add_argument("--init", default=None, help="start from these flat weights instead of Xavier")
+    ap.add_argument("--lr", type=float, default=1e-2, help="initial learning rate")
+    ap.add_argument("--val-nodes", type=int, default=50000,
+                    help="held-out star domain on which every round's weights are judged by FCG iterations")
     ap.add_argument("--out", default=None)
     ap.add_argument("--log", default=None)
     a = ap.parse_args()
@@ -47,7 +53,19 @@ def main():
         a.out = os.path.join(HERE, f"dss_k{KBAR}_d{D}.npy")
     log = open(a.log, "w") if a.log else sys.stdout
     ctx = ddg.ddg_create(0)
-    model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, None, seed=2024)
+    w0 = np.load(a.init).astype(np.float32) if a.init else None
+    model = ddg.ddg_model_create(ctx, KBAR, D, ALPHA, w0, seed=2024)
+    # held-out problem (seed disjoint from training, tests and benchmark): the kept weights are
+    # those whose DDM-GNN FCG reaches 1e-6 in the fewest iterations
+    vm = synth.star_mesh(a.val_nodes, seed=7001)
+    val = ddg.ddg_mesh_upload(ctx, vm.xy, vm.tri)
+    ddg.ddg_assemble_poly(val, synth.poly_coeffs(7001))
+    ddg.ddg_partition(val, max(1, int(round((vm.n - vm.n_boundary_ring) / 1000.0))), 2)
+
+    def val_iterations():
+        ddg.ddg_setup_precond(val, ddg.DDG_DDM_GNN, model, ddg.DDG_COARSE)
+        rep, _ = ddg.ddg_fcg_solve(val, 1e-6, 1000, 10, want_x=False)
+        return rep["iterations"] if rep["status"] == ddg.DDG_OK else 10 ** 6
     problems = []
     for s in range(a.meshes):
         seed = 5000 + s
@@ -57,9 +75,12 @@ def main():
         ddg.ddg_assemble_poly(p, synth.poly_coeffs(seed))
         ddg.ddg_partition(p, K, 2)
         problems.append(p)
-    lr, best, stale, rnd = 1e-2, np.inf, 0, 0
+    lr, best, stale, rnd = a.lr, np.inf, 0, 0
     t0 = time.time()
     n_w = KBAR * synth.n_weights_per_block(D)
+    best_it = val_iterations()
+    best_w = ddg.ddg_model_get_weights(model, n_w)
+    print(f"start: held-out FCG iterations {best_it}", file=log, flush=True)
     while time.time() - t0 < 60.0 * a.minutes:
         losses = []
         for i, p in enumerate(problems):
@@ -71,6 +92,10 @@ def main():
                   file=log, flush=True)
             if time.time() - t0 > 60.0 * a.minutes:
                 break
+        its = val_iterations()
+        if its < best_it:
+            best_it, best_w = its, ddg.ddg_model_get_weights(model, n_w)
+        print(f"round {rnd} held-out FCG iterations {its} (best {best_it})", file=log, flush=True)
         mean = float(np.mean(losses))
         if mean < 0.99 * best:
             best, stale = mean, 0
@@ -79,9 +104,9 @@ def main():
             if stale >= 2:
                 lr, stale = lr * 0.1, 0
         rnd += 1
-    np.save(a.out, ddg.ddg_model_get_weights(model, n_w))
-    print(f"saved {a.out} after {rnd} rounds", file=log, flush=True)
-    for p in problems:
+    np.save(a.out, best_w)
+    print(f"saved {a.out} after {rnd} rounds (held-out FCG iterations {best_it})", file=log, flush=True)
+    for p in problems + [val]:
         ddg.ddg_problem_destroy(p)
     ddg.ddg_model_destroy(model)
     ddg.ddg_destroy(ctx)
