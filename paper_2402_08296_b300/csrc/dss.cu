@@ -1441,16 +1441,38 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     // at least one node per thread: a small problem takes fewer CTAs (and leaves SMs to the
     // kernels of other streams) rather than slivers of a few nodes with large halos
     const long long cs = std::max<long long>(T, (n + slots * waves - 1) / (slots * waves));
-    const int nc = (int)((n + cs - 1) / cs);
-    std::vector<int> lp(K + 1), gid(n), cn0(nc), cown(nc);
+    const long long nc_target = (n + cs - 1) / cs;
+    std::vector<int> lp(K + 1), lk(K), nptr(n + K), gid(n), cn0, cown;
     DDG_CU(cudaMemcpyAsync(lp.data(), p->loc_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaMemcpyAsync(lk.data(), p->loc_nint, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    DDG_CU(cudaMemcpyAsync(nptr.data(), p->nbr_ptr, sizeof(int) * (n + K), cudaMemcpyDeviceToHost, s));
     DDG_CU(cudaStreamSynchronize(s));
+    // estimated instructions of a node in one block: projections and node MLPs, plus per
+    // neighbour the edge geometry and the out-message, and the in-message for unknowns
+    std::vector<double> work(n);
+    double total = 0.0;
     for (int g = 0; g < K; ++g)
-        for (int u = lp[g]; u < lp[g + 1]; ++u) gid[u] = g;
-    for (int q = 0; q < nc; ++q) {
-        cn0[q] = (int)(q * cs);
-        cown[q] = (int)std::min(cs, n - q * cs);
+        for (int u = lp[g]; u < lp[g + 1]; ++u) {
+            gid[u] = g;
+            const int j = u - lp[g];
+            const int deg = nptr[lp[g] + g + j + 1] - nptr[lp[g] + g + j];
+            work[u] = 500.0 + (j < lk[g] ? 95.0 : 60.0) * deg;
+            total += work[u];
+        }
+    // equal-work ranges (at most 2T nodes each), about nc_target of them
+    const double per = total / (double)nc_target;
+    double acc = 0.0;
+    long long start = 0;
+    for (long long u = 0; u < n; ++u) {
+        acc += work[u];
+        const long long len = u + 1 - start;
+        if (len == 2LL * T || acc >= per * (double)(cn0.size() + 1) || u == n - 1) {
+            cn0.push_back((int)start);
+            cown.push_back((int)len);
+            start = u + 1;
+        }
     }
+    const int nc = (int)cn0.size();
     cp.T = T;
     cp.global = true;
     cp.nchunks = nc;
