@@ -50,6 +50,8 @@ enum ddg_status {
     DDG_CUDA_ERROR = -3,    /* a CUDA runtime call failed */
     DDG_NOT_CONVERGED = -4, /* max_iter reached */
     DDG_BREAKDOWN = -5,     /* p.q <= 0 or a non-finite scalar in the Krylov loop */
+    DDG_BUSY = -6,          /* ddg_submit: the admission queue is full */
+    DDG_TIMEOUT = -7,       /* a kernel's bounded wait (about one second) ran out; the context stays usable */
     DDG_PENDING = -8,       /* ddg_poll: the request has not finished yet */
     DDG_BAD_MESH = -9,      /* degenerate or inverted triangle, or a node of too high degree */
     DDG_TOO_LARGE = -10     /* a subdomain or node list beyond a kernel's on-chip capacity */
@@ -259,7 +261,9 @@ int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, double *y_d
  * reproduces PCG for a fixed SPD preconditioner) from x0 (host, n_free, or
  * NULL = 0) until |r| / |b| < rtol or max_iter iterations.  x_host[n_nodes]
  * receives the full nodal solution (g on Dirichlet nodes).  Returns the
- * report's status. */
+ * report's status: DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN, or DDG_TIMEOUT
+ * when a kernel gave up a bounded wait during the solve (the context stays
+ * usable). */
 int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,
                       double *x_host, ddg_solve_report *report);
 
@@ -298,14 +302,16 @@ int32_t ddg_submit(ddg_ctx *ctx, int32_t n_nodes, const double *xy, int32_t n_tr
  * report (solve_ms = wall time from admission to the result) and, if x_host
  * is not NULL, the nodal solution (n_nodes).  A ticket is collected once. */
 int32_t ddg_poll(ddg_ctx *ctx, uint64_t ticket, ddg_solve_report *report, double *x_host);
-/* Most requests in flight at once (default 64), and whether concurrent DDM-GNN
- * requests share fused GNN launches (fuse_gnn = 1: each step advances every
- * member of a group by one FCG iteration, the members' subdomains in one launch
- * per message-passing block; 0, the default: every request runs its own
- * kernels on its own stream, its FCG periods replayed as CUDA graphs, and the
- * GPU overlaps the requests).  Results are the same either way.  Both settings
- * apply to requests started after the call. */
-int32_t ddg_serve_config(ddg_ctx *ctx, int32_t max_active, int32_t fuse_gnn);
+/* Most requests in flight at once (default 64), most requests waiting for
+ * admission (default 65536; ddg_submit returns DDG_BUSY beyond it), and whether
+ * concurrent DDM-GNN requests share fused GNN launches (fuse_gnn = 1: each step
+ * advances every member of a group by one FCG iteration, the members'
+ * subdomains in one launch per message-passing block; 0, the default: every
+ * request runs its own kernels on its own stream, its FCG periods replayed as
+ * CUDA graphs, and the GPU overlaps the requests).  Results are the same
+ * either way.  The settings apply to requests submitted or started after the
+ * call. */
+int32_t ddg_serve_config(ddg_ctx *ctx, int32_t max_active, int32_t fuse_gnn, int32_t max_pending);
 int32_t ddg_serve_stats(ddg_ctx *ctx, ddg_serve_summary *out);
 
 #ifdef __cplusplus

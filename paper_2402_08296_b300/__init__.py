@@ -31,6 +31,8 @@ DDG_OOM = -2
 DDG_CUDA_ERROR = -3
 DDG_NOT_CONVERGED = -4
 DDG_BREAKDOWN = -5
+DDG_BUSY = -6
+DDG_TIMEOUT = -7
 DDG_PENDING = -8
 DDG_BAD_MESH = -9
 DDG_TOO_LARGE = -10
@@ -115,7 +117,7 @@ _SIGS = {
     "ddg_train_loss_grad": [_p, _p, _p, _p, _i32, ctypes.POINTER(_f64), _p],
     "ddg_submit": [_p, _i32, _p, _i32, _p, _p, ctypes.POINTER(ddg_solve_opts), ctypes.POINTER(_u64)],
     "ddg_poll": [_p, _u64, ctypes.POINTER(ddg_solve_report), _p],
-    "ddg_serve_config": [_p, _i32, _i32],
+    "ddg_serve_config": [_p, _i32, _i32, _i32],
     "ddg_serve_stats": [_p, ctypes.POINTER(ddg_serve_summary)],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
 }
@@ -403,8 +405,8 @@ def ddg_poll(ctx, ticket: int, n_nodes: int | None = None):
     return st, rep.as_dict(), x
 
 
-def ddg_serve_config(ctx, max_active: int, fuse_gnn: bool = False) -> None:
-    _check(lib.ddg_serve_config(ctx, max_active, 1 if fuse_gnn else 0), "ddg_serve_config")
+def ddg_serve_config(ctx, max_active: int, fuse_gnn: bool = False, max_pending: int = 65536) -> None:
+    _check(lib.ddg_serve_config(ctx, max_active, 1 if fuse_gnn else 0, max_pending), "ddg_serve_config")
 
 
 def ddg_serve_stats(ctx) -> dict:

@@ -46,6 +46,7 @@ enum : int {
     ST_BAD_MESH = 1,      // non-positive triangle area, node degree over the cap
     ST_TOO_LARGE = 2,     // list longer than a kernel's local capacity
     ST_BAD_INPUT = 4,     // user partition value out of range
+    ST_TIMEOUT = 8,       // a bounded wait ran out
 };
 
 constexpr int MAX_NODE_TRI = 32;   // triangles around one node

@@ -18,6 +18,7 @@
 #include "dss_layout.cuh"
 
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 
 #include <cmath>
@@ -275,6 +276,7 @@ struct DssArgs {
     int nmax, emax;         // shared-memory capacity in nodes and edges
     const int *stop;        // optional: skip all work when *stop != 0
     int *status;
+    int test_skip_copy;     // failure test: never issue the first weight copy, so the bounded wait runs out
 };
 
 template <int P>
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) bulk_load(Wbuf, a.weights, BLOCK_BYTES, &bar[0]);
+    if (tid == 0 && !a.test_skip_copy) bulk_load(Wbuf, a.weights, BLOCK_BYTES, &bar[0]);
     // stage the graph
     for (int q = tid; q < nl; q += DSS_THREADS) xy[q] = a.loc_xy[lp + q];
     for (int q = tid; q <= nl; q += DSS_THREADS) nptr[q] = (uint16_t)gptr[q];
@@ -324,13 +326,20 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
         for (int o = 0; o < D; ++o) h[p][o] = 0.f;
     }
     const float alpha = a.alpha;
-    bool ok = true;
 
     for (int blk = 0; blk < a.kbar; ++blk) {
         const int buf = blk & 1;
         const float *W = Wbuf + buf * BLOCK_FLOATS;
-        if (!mbar_wait(&bar[buf], (uint32_t)((blk >> 1) & 1))) ok = false;
-        __syncthreads();
+        const bool late = !mbar_wait(&bar[buf], (uint32_t)((blk >> 1) & 1));
+        if (__syncthreads_or(late)) {
+            // the weight copy did not arrive within about a second: report, give the copy one more
+            // bounded wait (it must not land in shared memory this CTA no longer owns), and stop
+            if (tid == 0) {
+                raise_status(a.status, ST_TIMEOUT);
+                if (!a.test_skip_copy || blk > 0) mbar_wait(&bar[buf], (uint32_t)((blk >> 1) & 1));
+            }
+            return;
+        }
         if (tid == 0 && blk + 1 < a.kbar)
             bulk_load(Wbuf + (buf ^ 1) * BLOCK_FLOATS, a.weights + (size_t)(blk + 1) * BLOCK_FLOATS, BLOCK_BYTES,
                       &bar[buf ^ 1]);
@@ -414,7 +423,6 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss(DssArgs a) {
         }
         __syncthreads();
     }
-    if (!ok && tid == 0) raise_status(a.status, ST_TOO_LARGE);
     // decoder of the last block on the unknowns (Eq. 22)
     const float *W = Wbuf + ((a.kbar - 1) & 1) * BLOCK_FLOATS;
 #pragma unroll
@@ -1787,6 +1795,7 @@ int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaSt
     a.emax = p->max_edges;
     a.stop = stop;
     a.status = p->d_status;
+    a.test_skip_copy = getenv("DDG_TEST_WAIT_TIMEOUT") != nullptr;  // failure test only
     size_t smem = dss_smem_bytes(a.nmax, a.emax);
     int P = cdiv(p->max_loc, DSS_THREADS);
     switch (P) {

@@ -119,9 +119,16 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
-// bounded wait on a phase of an mbarrier; returns false if the bound ran out
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait on a phase of an mbarrier for at most about one second; returns false if that ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -129,8 +136,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > 1000000000ull) return false;
     }
-    return false;
 }
 
 template <int NIN>

@@ -785,8 +785,12 @@ struct FcgRun {
         rp.gnn_schedule = p->kind == DDG_DDM_GNN ? p->dss_sched : -1;
         rp.gnn_chunk_t = (p->kind == DDG_DDM_GNN && p->dss_sched >= 2) ? p->chunk.T : 0;
         rp.status = hflag[F_STOP] == 1 ? DDG_OK : (hflag[F_STOP] == 2 ? DDG_BREAKDOWN : DDG_NOT_CONVERGED);
+        // a kernel that gave up a bounded wait (or met another device-side error) overrides the outcome
+        const int32_t dev = check_status(p, "FCG solve");
+        if (dev != DDG_OK) rp.status = dev;
         if (rep) *rep = rp;
         release();
+        if (dev != DDG_OK) return dev;
         if (rp.status == DDG_BREAKDOWN) set_error("FCG breakdown: p.q <= 0 or a non-finite scalar");
         if (rp.status == DDG_NOT_CONVERGED) set_error("FCG reached max_iter");
         return rp.status;

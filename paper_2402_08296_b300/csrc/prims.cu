@@ -55,6 +55,10 @@ int32_t check_status(ddg_problem *p, const char *where) {
         set_error(w + ": degenerate/inverted triangle or node degree above the cap");
         return DDG_BAD_MESH;
     }
+    if (st & ST_TIMEOUT) {
+        set_error(w + ": a kernel's bounded wait for its data ran out");
+        return DDG_TIMEOUT;
+    }
     if (st & ST_TOO_LARGE) {
         set_error(w + ": a list exceeds a kernel's capacity");
         return DDG_TOO_LARGE;

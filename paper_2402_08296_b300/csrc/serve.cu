@@ -76,6 +76,7 @@ struct Server {
     bool stop = false;
     uint64_t next_ticket = 1;
     int max_active = 64;
+    int max_pending = 65536;
     size_t reserved = 0;
     std::vector<double> latencies;
     uint64_t completed = 0, failed = 0;
@@ -385,15 +386,16 @@ using namespace ddg;
 
 extern "C" {
 
-int32_t ddg_serve_config(ddg_ctx *c, int32_t max_active, int32_t fuse_gnn) {
+int32_t ddg_serve_config(ddg_ctx *c, int32_t max_active, int32_t fuse_gnn, int32_t max_pending) {
     clear_error();
-    if (!c || max_active < 1 || (fuse_gnn != 0 && fuse_gnn != 1)) {
+    if (!c || max_active < 1 || (fuse_gnn != 0 && fuse_gnn != 1) || max_pending < 1) {
         set_error("ddg_serve_config: bad arguments");
         return DDG_INVALID_ARG;
     }
     Server *S = server_get(c);
     std::lock_guard<std::mutex> lock(S->mu);
     S->max_active = max_active;
+    S->max_pending = max_pending;
     // the scheduler reads `fuse` when it starts a request: switching only affects later ones
     S->fuse = fuse_gnn != 0 && S->fuse_ready;
     return DDG_OK;
@@ -420,6 +422,11 @@ int32_t ddg_submit(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n_tri,
     q->t_submit = now_ms();
     Server *S = server_get(c);
     std::lock_guard<std::mutex> lock(S->mu);
+    if ((int)S->pending.size() >= S->max_pending) {
+        delete q;
+        set_error("ddg_submit: the admission queue is full");
+        return DDG_BUSY;
+    }
     q->ticket = S->next_ticket++;
     S->live.insert(q->ticket);
     if (S->t_first_submit < 0.0) S->t_first_submit = q->t_submit;

@@ -98,3 +98,25 @@ def test_admission_waits_for_the_hbm_budget():
         assert peak <= budget
     finally:
         ddg.ddg_destroy(ctx)
+
+
+def test_a_full_admission_queue_answers_busy():
+    import paper_2402_08296_b300 as ddg
+    ctx = ddg.ddg_create(0)
+    try:
+        ddg.ddg_serve_config(ctx, 1, max_pending=2)
+        mesh = synth.star_mesh(20000, seed=500)
+        r = synth.poly_coeffs(500)
+        got, busy = [], 0
+        for _ in range(8):   # submitted faster than one slot drains them
+            try:
+                got.append(ddg.ddg_submit(ctx, mesh.xy, mesh.tri, r, ddg.DDG_DDM_LU, max_iter=400))
+            except ddg.DdgError as e:
+                assert e.status == ddg.DDG_BUSY
+                busy += 1
+        assert busy > 0 and len(got) >= 2
+        res = _wait(ddg, ctx, got, [mesh.n] * len(got))
+        assert all(st == ddg.DDG_OK for st, _, _ in res.values())
+    finally:
+        ddg.ddg_destroy(ctx)
+

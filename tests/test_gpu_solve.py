@@ -163,3 +163,27 @@ def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, schedule,
     finally:
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)
+
+
+def test_a_weight_copy_that_never_arrives_ends_in_a_timeout_status(ddg, ctx, monkeypatch):
+    """The persistent GNN kernel waits about one second for each block's weights (bulk copy and
+    mbarrier); a test hook withholds the first copy, so every CTA's wait runs out.  The solve
+    reports DDG_TIMEOUT, and the context is usable afterwards.  No fault, trap or hang."""
+    w = synth.workload("square2k", 4)
+    W = synth.dss_weights(30, 10, 4)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
+    try:
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", "0")
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        monkeypatch.setenv("DDG_TEST_WAIT_TIMEOUT", "1")
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_fcg_solve(p, 1e-6, 1, 10)
+        assert e.value.status == ddg.DDG_TIMEOUT
+        monkeypatch.delenv("DDG_TEST_WAIT_TIMEOUT")
+        rep, _ = ddg.ddg_fcg_solve(p, 1e-6, 300, 10)
+        assert rep["status"] == ddg.DDG_OK
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
