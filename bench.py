@@ -264,8 +264,12 @@ def run_ours(a, rank, world, local_rank):
         ddg.ddg_local_corrections(p, r_dev, corr, s_dev)
     eb.record(cur)
     torch.cuda.synchronize()
-    local_ms = ea.elapsed_time(eb)
-    local_launches = n_app
+    standalone_ms = ea.elapsed_time(eb) / n_app
+    # the roofline uses the CUDA events recorded around the GNN's launches inside the timed solves
+    # (on the library's stream, in the captured FCG periods); the stand-alone loop above, launched
+    # call by call from the host, is reported beside it
+    local_ms = in_solve_ms
+    local_launches = 1
 
     tot_gnn = max_over_ranks(float(t_gnn.sum()) / 1e3)
     tot_lu = max_over_ranks(float(t_lu.sum()) / 1e3)
@@ -317,9 +321,8 @@ def run_ours(a, rank, world, local_rank):
                      "traffic_unit": "bytes per application (ncu capture, warm L2)",
                      "flops_per_application": flops, "nodes": nodes, "messages": msgs,
                      "avg_application_ms": avg_launch_s * 1e3,
-                     "application_timing": "20 back-to-back local-solve applications (restriction + GNN "
-                                           "launches + corrections copy), CUDA events",
-                     "in_solve_application_ms": in_solve_ms,
+                     "application_timing": "CUDA events around the GNN launches inside the timed solves",
+                     "standalone_application_ms": standalone_ms,
                      "gnn_schedule": r_gnn[0]["gnn_schedule"], "gnn_chunk_t": r_gnn[0]["gnn_chunk_t"],
                      "kernel_launches_per_application": r_gnn[0]["local_launches"] // max(1, r_gnn[0]["local_applies"]),
                      "peak_note": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (unit counts and max clock)"},

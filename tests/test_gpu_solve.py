@@ -181,6 +181,11 @@ def test_a_weight_copy_that_never_arrives_ends_in_a_timeout_status(ddg, ctx, mon
             ddg.ddg_fcg_solve(p, 1e-6, 1, 10)
         assert e.value.status == ddg.DDG_TIMEOUT
         monkeypatch.delenv("DDG_TEST_WAIT_TIMEOUT")
+        # usable afterwards: the same GNN runs to its iteration cap (untrained weights), and a
+        # DDM-LU solve on the same problem converges
+        rep, _ = ddg.ddg_fcg_solve(p, 1e-6, 20, 10)
+        assert rep["status"] in (ddg.DDG_OK, ddg.DDG_NOT_CONVERGED) and rep["iterations"] >= 1
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE)
         rep, _ = ddg.ddg_fcg_solve(p, 1e-6, 300, 10)
         assert rep["status"] == ddg.DDG_OK
     finally:
