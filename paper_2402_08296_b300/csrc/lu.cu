@@ -180,14 +180,27 @@ __global__ void __launch_bounds__(LU_T) k_lu_factor(const int *sub_ptr, const in
 }
 
 // forward and backward band solves, one CTA per subdomain, rows in tiles of 32:
-// a warp solves each 32 x 32 diagonal tile, the whole CTA applies the band
-// entries outside it; corr is written in sub_idx order
+// the CTA stages each 32 x 32 diagonal tile of the factor in shared memory with
+// coalesced loads, a warp solves it from there, and the whole CTA applies the
+// band entries outside it; corr is written in sub_idx order
 constexpr int LU_TILE = 32;
+
+// Ds[rr][cc] = L[r0 + rr][r0 + cc] inside the band (diagonal slot: 1 / L_rr), 0 elsewhere
+__device__ __forceinline__ void lu_stage_tile(double (*Ds)[LU_TILE + 1], const double *B, int w, int bw, int r0,
+                                              int nrow) {
+    for (int q = threadIdx.x; q < LU_TILE * LU_TILE; q += LU_T) {
+        const int rr = q / LU_TILE, cc = q % LU_TILE;
+        double v = 0.0;
+        if (rr < nrow && cc <= rr && rr - cc <= bw) v = B[(long long)(r0 + rr) * w + (cc - rr + bw)];
+        Ds[rr][cc] = v;
+    }
+}
 
 __global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int *sub_idx, const int *lu_pos,
                                                    const int *bw_arr, const long long *off, const double *band,
                                                    const double *r, const double *s, double *corr, const int *stop) {
     extern __shared__ double yv[];
+    __shared__ double Ds[LU_TILE][LU_TILE + 1];
     if (stop && *stop) return;
     const int i = blockIdx.x;
     const int s0 = sub_ptr[i], k = sub_ptr[i + 1] - s0;
@@ -211,15 +224,15 @@ __global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) yv[row] -= acc;
         }
+        lu_stage_tile(Ds, B, w, bw, r0, nrow);
         __syncthreads();
         if (warp == 0) {
             const int row = r0 + lane;
-            const double *Lr = B + (long long)row * w;
             double y = lane < nrow ? yv[row] : 0.0;
             for (int j = 0; j < nrow; ++j) {
-                if (lane == j) y *= Lr[bw];
+                if (lane == j) y *= Ds[j][j];
                 const double xj = __shfl_sync(0xffffffffu, y, j);
-                if (lane > j && lane < nrow && lane - j <= bw) y -= Lr[(r0 + j) - row + bw] * xj;
+                if (lane > j && lane < nrow && lane - j <= bw) y -= Ds[lane][j] * xj;
             }
             if (lane < nrow) yv[row] = y;
         }
@@ -228,14 +241,16 @@ __global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int
     // L^T x = y, tiles from the bottom
     for (int r0 = ((k - 1) / LU_TILE) * LU_TILE; r0 >= 0; r0 -= LU_TILE) {
         const int nrow = min(LU_TILE, k - r0);
+        lu_stage_tile(Ds, B, w, bw, r0, nrow);
+        __syncthreads();
         if (warp == 0) {
             const int row = r0 + lane;
             double y = lane < nrow ? yv[row] : 0.0;
-            const double dinv = lane < nrow ? B[(long long)row * w + bw] : 0.0;
+            const double dinv = lane < nrow ? Ds[lane][lane] : 0.0;
             for (int j = nrow - 1; j >= 0; --j) {
                 if (lane == j) y *= dinv;
                 const double xj = __shfl_sync(0xffffffffu, y, j);
-                if (lane < j && j - lane <= bw) y -= B[(long long)(r0 + j) * w + (row - (r0 + j) + bw)] * xj;
+                if (lane < j && j - lane <= bw) y -= Ds[j][lane] * xj;
             }
             if (lane < nrow) yv[row] = y;
         }
