@@ -111,7 +111,8 @@ struct ChunkPlan {
     bool global = false;  // schedule 3: chunks are ranges of the concatenated graphs' nodes, sized to fill
                           // the GPU evenly; own nodes sorted by message count, neighbour kind in bit 15
     int *gid = nullptr;   // global: graph of every local node (sum_loc)
-    int4 *info = nullptr; // global: per own slot {node, corr index or -1, free index of r or -1, graph}
+    int4 *info = nullptr; // global: per own slot {node, corr index or -1, free index of r or -1,
+                          //   graph | out-messages << 24}
     int *c_graph = nullptr, *c_n0 = nullptr, *c_own = nullptr, *c_need_off = nullptr, *c_need_n = nullptr;
     int *need = nullptr, *c_adj_off = nullptr, *adj_ptr = nullptr, *c_adj_base = nullptr;
     uint16_t *adj = nullptr;

@@ -648,7 +648,7 @@ struct ChunkArgs {
     const int *c_adj_base;                  // per chunk: start of its slice in adj
     const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
     const int *gid;                         // global plans: graph of every local node
-    const int4 *info;                       // global plans: per own slot {node, corr idx, r idx, graph}
+    const int4 *info;                       // global plans: per own slot {node, corr idx, r idx, graph | dout << 24}
     const float2 *loc_xy;
     const double *r, *s;
     double *corr;
@@ -876,7 +876,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
     const int *APTR = a.adj_ptr + a.c_adj_off[q];      // [own + 1]
     const uint16_t *ADJ = a.adj + a.c_adj_base[q];     // chunk-local ids, bit 15: neighbour is an unknown
-    const int4 *INFO = a.info + a.c_n0[q];             // [own] {node, corr idx, r idx, graph}
+    const int4 *INFO = a.info + a.c_n0[q];             // [own] {node, corr idx, r idx, graph | dout << 24}
     float4 *Pb = smem4;                                               // [nn][5]
     float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
@@ -887,14 +887,14 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     // phase A: projections and coordinates of every needed node
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
-        float h[D], cdummy;
-        if (first) {
+        if (first) {  // h = 0: the projections vanish
 #pragma unroll
-            for (int o = 0; o < D; ++o) h[o] = 0.f;
+            for (int m = 0; m < D / 2; ++m) Pb[(size_t)u * 5 + m] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
+            float h[D], cdummy;
             load_hrow(hrow_in, node, h, cdummy);
+            fused_project<T>(W, h, Pb + (size_t)u * 5);
         }
-        fused_project<T>(W, h, Pb + (size_t)u * 5);
         XY[u] = a.loc_xy[node];
     }
     __syncthreads();
@@ -909,7 +909,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
         if (first) {
 #pragma unroll
             for (int o = 0; o < D; ++o) hp[o] = 0.f;
-            const double s = a.s[inf.w];
+            const double s = a.s[inf.w & 0xffffff];
             c = (inner && s != 0.0) ? (float)(a.r[inf.z] / s) : 0.f;
         } else {
             load_hrow(hrow_in, node, hp, c);
@@ -917,7 +917,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
         const float2 xj = XY[u];
         const int e0 = APTR[u], e1 = APTR[u + 1];
         f2_t so[D / 2], si[D / 2], pao[D / 2], pai[D / 2];
-        float dout = 0.f;
+        const float dout = (float)((unsigned)inf.w >> 24);  // out-messages (neighbours that are unknowns)
 #pragma unroll
         for (int m = 0; m < D / 2; ++m) {
             so[m] = 0ull;
@@ -931,7 +931,6 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
             const unsigned ent = ADJ[e];
             const int v = ent & 0x7fffu;
             const float mo = (float)(ent >> 15);
-            dout += mo;
             const float2 xl = XY[v];
             const float dx = xl.x - xj.x, dy = xl.y - xj.y;
             const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
@@ -1005,7 +1004,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
                     y = fmaf(W.w[F_DW2 + 2 * m], relu(d0), y);
                     y = fmaf(W.w[F_DW2 + 2 * m + 1], relu(d1), y);
                 }
-                const double s = a.s[inf.w];
+                const double s = a.s[inf.w & 0xffffff];
                 a.corr[inf.y] = s == 0.0 ? 0.0 : s * (double)y;
             }
         } else {
@@ -1179,7 +1178,14 @@ __global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int
         const int j = u - loc_ptr[g];
         const bool in = j < loc_nint[g];
         nd[r] = u;
-        info[o0 + r] = make_int4(u, in ? sub_ptr[g] + j : -1, in ? sub_idx[sub_ptr[g] + j] : -1, g);
+        int dout = 0;  // out-messages per block: neighbours that are unknowns
+        {
+            const int *gptr = nbr_ptr + loc_ptr[g] + g;
+            const uint16_t *gn = nbr + nbr_off[g];
+            for (int e = gptr[j]; e < gptr[j + 1]; ++e) dout += gn[e] < loc_nint[g] ? 1 : 0;
+        }
+        info[o0 + r] = make_int4(u, in ? sub_ptr[g] + j : -1, in ? sub_idx[sub_ptr[g] + j] : -1,
+                                 g | (min(dout, 255) << 24));
     }
     for (int t = threadIdx.x; t < ext; t += NT) nd[own + t] = cand[t];
     for (int r = threadIdx.x; r <= own; r += NT) ap[r] = sptr[r];
