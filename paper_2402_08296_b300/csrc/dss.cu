@@ -106,6 +106,16 @@ static void fuse_block(const float *w, const FlatOffsets &fo, float alpha, float
     }
     o[F_DB2] = db2[0];
     o[F_DB2 + 1] = 0.f;
+    // position rows (x, y) of the two edge MLPs' We, with the in-message's sign folded as in WEI
+    for (int c = 0; c < 2; ++c)
+        for (int m = 0; m < D / 2; ++m)
+            for (int t = 0; t < 4; ++t)
+                o[F_XB + c * 2 * D + 4 * m + t] = t < 2 ? o[F_WEO + c * D + 2 * m + t] : o[F_WEI + c * D + 2 * m + t - 2];
+    for (int c = 0; c < 2; ++c)
+        for (int q = 0; q < D; ++q) {
+            o[F_NXA + c * 2 * D + q] = -o[F_WEO + c * D + q];
+            o[F_NXA + c * 2 * D + D + q] = -o[F_WEI + c * D + q];
+        }
 }
 
 // both host layouts (padded per-block, composed per-block) from flat weights
@@ -803,11 +813,15 @@ __global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid
 // branched over.  Shared memory: per needed node its neighbour projections as
 // five float4 (Wb_out h pair m, Wb_in h pair m) and its scaled coordinates.
 template <int T>
-__device__ __forceinline__ void fused_project(const FusedWeights &W, const float (&h)[D], float4 *dst) {
+__device__ __forceinline__ void fused_project(const FusedWeights &W, const float (&h)[D], float2 xy, float4 *dst) {
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     f2_t acc[D];
+    {
+        const f2_t x2 = f2_pack(xy.x, xy.x), y2 = f2_pack(xy.y, xy.y);
 #pragma unroll
-    for (int q = 0; q < D; ++q) acc[q] = 0ull;
+        for (int q = 0; q < D; ++q)
+            acc[q] = f2_fma(Wp[(F_XB + 2 * D) / 2 + q], y2, f2_fma(Wp[F_XB / 2 + q], x2, 0ull));
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         const f2_t xi = f2_pack(h[i], h[i]);
@@ -843,15 +857,14 @@ __device__ __forceinline__ void f2_mv(f2_t (&acc)[D / 2], const f2_t *Wp, const 
     }
 }
 
-// one message pair-block: acc += mask * relu(pa + pb + We e) over the five output pairs
+// one message pair-block with the position terms already in pa and pb:
+// acc += mask * relu(pa + pb + We_|d| |d|)
 template <int OFF_WE, bool MASKED>
-__device__ __forceinline__ void f2_msg(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 2], const f2_t (&pb)[D / 2],
-                                       const f2_t *Wp, f2_t dx2, f2_t dy2, f2_t dn2, f2_t mask2) {
+__device__ __forceinline__ void f2_msg_n(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 2], const f2_t (&pb)[D / 2],
+                                         const f2_t *Wp, f2_t dn2, f2_t mask2) {
 #pragma unroll
     for (int m = 0; m < D / 2; ++m) {
         f2_t z = f2_add(pa[m], pb[m]);
-        z = f2_fma(Wp[OFF_WE / 2 + m], dx2, z);
-        z = f2_fma(Wp[(OFF_WE + D) / 2 + m], dy2, z);
         z = f2_fma(Wp[(OFF_WE + 2 * D) / 2 + m], dn2, z);
         acc[m] = MASKED ? f2_fma(f2_relu(z), mask2, acc[m]) : f2_add(acc[m], f2_relu(z));
     }
@@ -887,15 +900,16 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     // phase A: projections and coordinates of every needed node
     for (int u = tid; u < nn; u += T) {
         const int node = need[u];
-        if (first) {  // h = 0: the projections vanish
+        const float2 xy = a.loc_xy[node];
+        float h[D], cdummy;
+        if (first) {  // h = 0: only the position terms remain
 #pragma unroll
-            for (int m = 0; m < D / 2; ++m) Pb[(size_t)u * 5 + m] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int o = 0; o < D; ++o) h[o] = 0.f;
         } else {
-            float h[D], cdummy;
             load_hrow(hrow_in, node, h, cdummy);
-            fused_project<T>(W, h, Pb + (size_t)u * 5);
         }
-        XY[u] = a.loc_xy[node];
+        fused_project<T>(W, h, xy, Pb + (size_t)u * 5);
+        XY[u] = xy;
     }
     __syncthreads();
 #pragma unroll
@@ -927,6 +941,14 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
         }
         f2_mv<F_HA, 3 * D>(pao, Wp, hp);
         if (inner) f2_mv<F_HA + D, 3 * D>(pai, Wp, hp);
+        {
+            const f2_t x2 = f2_pack(xj.x, xj.x), y2 = f2_pack(xj.y, xj.y);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                pao[m] = f2_fma(Wp[(F_NXA + 2 * D) / 2 + m], y2, f2_fma(Wp[F_NXA / 2 + m], x2, pao[m]));
+                pai[m] = f2_fma(Wp[(F_NXA + 3 * D) / 2 + m], y2, f2_fma(Wp[(F_NXA + D) / 2 + m], x2, pai[m]));
+            }
+        }
         for (int e = e0; e < e1; ++e) {
             const unsigned ent = ADJ[e];
             const int v = ent & 0x7fffu;
@@ -934,7 +956,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
             const float2 xl = XY[v];
             const float dx = xl.x - xj.x, dy = xl.y - xj.y;
             const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-            const f2_t dx2 = f2_pack(dx, dx), dy2 = f2_pack(dy, dy), dn2 = f2_pack(dn, dn);
+            const f2_t dn2 = f2_pack(dn, dn);
             f2_t po[D / 2], pi[D / 2];
 #pragma unroll
             for (int m = 0; m < D / 2; ++m) {  // one 16-byte shared load per output pair of both messages
@@ -942,8 +964,8 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
                 po[m] = f2_pack(t.x, t.y);
                 pi[m] = f2_pack(t.z, t.w);
             }
-            f2_msg<F_WEO, true>(so, pao, po, Wp, dx2, dy2, dn2, f2_pack(mo, mo));
-            if (inner) f2_msg<F_WEI, false>(si, pai, pi, Wp, dx2, dy2, dn2, 0ull);
+            f2_msg_n<F_WEO, true>(so, pao, po, Wp, dn2, f2_pack(mo, mo));
+            if (inner) f2_msg_n<F_WEI, false>(si, pai, pi, Wp, dn2, 0ull);
         }
         const float din = inner ? (float)(e1 - e0) : 0.f;
         // Psi hidden layer on [h, c, phi_out, phi_in] with the second message layers composed in

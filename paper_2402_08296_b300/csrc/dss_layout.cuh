@@ -64,8 +64,16 @@ constexpr int F_DW1 = F_PB2 + D;
 constexpr int F_DB1 = F_DW1 + D * D;
 constexpr int F_DW2 = F_DB1 + D;
 constexpr int F_DB2 = F_DW2 + D;
-constexpr int F_FLOATS = F_DB2 + 2;  // 1052
-static_assert(F_FLOATS % 2 == 0 && F_HA % 2 == 0 && F_MO % 2 == 0 && F_P2 % 2 == 0 && F_DW1 % 2 == 0,
+// the position part of the edge features, moved into per-node terms (schedule 3):
+//   We (x_l - x_j) = We x_l - We x_j, so the neighbour projection gains We x_l and the own-node
+//   term loses We x_j; only We_|d| |d| stays on the edge.
+//   XB  [2][2D]  rows x, y of We_out and We_in interleaved like HB (added to a neighbour's projections)
+//   NXA [2][2D]  rows x, y of -We_out | -We_in (added to the own node's first-layer terms)
+constexpr int F_XB = F_DB2 + 2;
+constexpr int F_NXA = F_XB + 2 * 2 * D;
+constexpr int F_FLOATS = F_NXA + 2 * 2 * D;  // 1132
+static_assert(F_FLOATS % 2 == 0 && F_HA % 2 == 0 && F_MO % 2 == 0 && F_P2 % 2 == 0 && F_DW1 % 2 == 0 &&
+                  F_XB % 2 == 0 && F_NXA % 2 == 0,
               "every pair starts on an 8-byte boundary");
 
 struct alignas(16) FusedWeights {
