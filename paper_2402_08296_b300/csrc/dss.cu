@@ -898,18 +898,34 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     // set-up data only; wait here until the previous launch's latents are complete and visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
     // phase A: projections and coordinates of every needed node
-    for (int u = tid; u < nn; u += T) {
-        const int node = need[u];
-        const float2 xy = a.loc_xy[node];
+    // software-pipelined: the next node's latent row and coordinates are loaded while this one is
+    // projected (phase A holds far fewer live values than phase B, so this costs no occupancy)
+    {
         float h[D], cdummy;
-        if (first) {  // h = 0: only the position terms remain
+        float2 xy = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int o = 0; o < D; ++o) h[o] = 0.f;
-        } else {
-            load_hrow(hrow_in, node, h, cdummy);
+        for (int o = 0; o < D; ++o) h[o] = 0.f;
+        if (tid < nn) {
+            const int node = need[tid];
+            xy = a.loc_xy[node];
+            if (!first) load_hrow(hrow_in, node, h, cdummy);
         }
-        fused_project<T>(W, h, xy, Pb + (size_t)u * 5);
-        XY[u] = xy;
+        for (int u = tid; u < nn; u += T) {
+            float hn[D];
+            float2 xyn = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < D; ++o) hn[o] = 0.f;
+            if (u + T < nn) {
+                const int nnode = need[u + T];
+                xyn = a.loc_xy[nnode];
+                if (!first) load_hrow(hrow_in, nnode, hn, cdummy);
+            }
+            fused_project<T>(W, h, xy, Pb + (size_t)u * 5);  // (h = 0 in the first block)
+            XY[u] = xy;
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = hn[o];
+            xy = xyn;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -949,8 +965,11 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
                 pai[m] = f2_fma(Wp[(F_NXA + 3 * D) / 2 + m], y2, f2_fma(Wp[(F_NXA + D) / 2 + m], x2, pai[m]));
             }
         }
+        // the next neighbour's entry is loaded one iteration ahead (its global load overlaps this edge)
+        unsigned ent_next = e0 < e1 ? ADJ[e0] : 0u;
         for (int e = e0; e < e1; ++e) {
-            const unsigned ent = ADJ[e];
+            const unsigned ent = ent_next;
+            if (e + 1 < e1) ent_next = ADJ[e + 1];
             const int v = ent & 0x7fffu;
             const float mo = (float)(ent >> 15);
             const float2 xl = XY[v];
