@@ -870,10 +870,11 @@ __device__ __forceinline__ void f2_msg_n(f2_t (&acc)[D / 2], const f2_t (&pa)[D 
     }
 }
 
-// shared memory of one chunk: the neighbour projections (five float4) and the
-// scaled coordinates (float2) of each of its nn needed nodes
-__host__ __device__ __forceinline__ size_t fused_smem(int nn) {
-    return (size_t)nn * (5 * sizeof(float4) + sizeof(float2));
+// shared memory of one chunk: per needed node its neighbour projections (five float4) and
+// scaled coordinates (float2); per own node its latent row (three float4, copied from the
+// loads of the projection phase for phase B)
+__host__ __device__ __forceinline__ size_t fused_smem(int nn, int own) {
+    return (size_t)nn * 5 * sizeof(float4) + (size_t)own * 3 * sizeof(float4) + (size_t)nn * sizeof(float2);
 }
 
 // One CTA of schedule 3 on chunk q of the plan in `a`; first/last mark the first and last
@@ -891,7 +892,8 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     const uint16_t *ADJ = a.adj + a.c_adj_base[q];     // chunk-local ids, bit 15: neighbour is an unknown
     const int4 *INFO = a.info + a.c_n0[q];             // [own] {node, corr idx, r idx, graph | dout << 24}
     float4 *Pb = smem4;                                               // [nn][5]
-    float2 *XY = reinterpret_cast<float2 *>(smem4 + (size_t)nn * 5);  // [nn]
+    float4 *HS = Pb + (size_t)nn * 5;                                 // [own][3] latent rows of own nodes
+    float2 *XY = reinterpret_cast<float2 *>(HS + (size_t)own * 3);    // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     const float4 *hrow_in = reinterpret_cast<const float4 *>(h_in);  // rows of 12: h[10], c, 0
     // launched as a programmatic dependent of the previous block: everything above reads
@@ -901,29 +903,35 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     // software-pipelined: the next node's latent row and coordinates are loaded while this one is
     // projected (phase A holds far fewer live values than phase B, so this costs no occupancy)
     {
-        float h[D], cdummy;
+        float h[D], cl = 0.f;
         float2 xy = make_float2(0.f, 0.f);
 #pragma unroll
         for (int o = 0; o < D; ++o) h[o] = 0.f;
         if (tid < nn) {
             const int node = need[tid];
             xy = a.loc_xy[node];
-            if (!first) load_hrow(hrow_in, node, h, cdummy);
+            if (!first) load_hrow(hrow_in, node, h, cl);
         }
         for (int u = tid; u < nn; u += T) {
-            float hn[D];
+            float hn[D], cn = 0.f;
             float2 xyn = make_float2(0.f, 0.f);
 #pragma unroll
             for (int o = 0; o < D; ++o) hn[o] = 0.f;
             if (u + T < nn) {
                 const int nnode = need[u + T];
                 xyn = a.loc_xy[nnode];
-                if (!first) load_hrow(hrow_in, nnode, hn, cdummy);
+                if (!first) load_hrow(hrow_in, nnode, hn, cn);
             }
             fused_project<T>(W, h, xy, Pb + (size_t)u * 5);  // (h = 0 in the first block)
             XY[u] = xy;
+            if (u < own) {  // own nodes keep their row for phase B
+                HS[3 * (size_t)u] = make_float4(h[0], h[1], h[2], h[3]);
+                HS[3 * (size_t)u + 1] = make_float4(h[4], h[5], h[6], h[7]);
+                HS[3 * (size_t)u + 2] = make_float4(h[8], h[9], cl, 0.f);
+            }
 #pragma unroll
             for (int o = 0; o < D; ++o) h[o] = hn[o];
+            cl = cn;
             xy = xyn;
         }
     }
@@ -935,14 +943,14 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
         const int4 inf = INFO[u];
         const int node = inf.x;
         const bool inner = inf.y >= 0;
-        float hp[D], c;  // read again (a cache hit) rather than held across the barrier
+        float hp[D], c;  // from the copy phase A left in shared memory
         if (first) {
 #pragma unroll
             for (int o = 0; o < D; ++o) hp[o] = 0.f;
             const double s = a.s[inf.w & 0xffffff];
             c = (inner && s != 0.0) ? (float)(a.r[inf.z] / s) : 0.f;
         } else {
-            load_hrow(hrow_in, node, hp, c);
+            load_hrow(HS, u, hp, c);
         }
         const float2 xj = XY[u];
         const int e0 = APTR[u], e1 = APTR[u + 1];
@@ -1485,7 +1493,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     const int K = p->K;
     int sms = 0, per_sm = 0;
     DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t smem_est = fused_smem(3 * T);  // 2T own + T outside nodes
+    const size_t smem_est = fused_smem(3 * T, 2 * T);  // 2T own + T outside nodes
     switch (T) {
         case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
         case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
@@ -1565,7 +1573,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
         ta += ha[q];
         tp += cown[q] + 1;
         maxn = std::max(maxn, hn[q]);
-        max_smem = std::max(max_smem, fused_smem(hn[q]));
+        max_smem = std::max(max_smem, fused_smem(hn[q], cown[q]));
     }
     cp.max_need = maxn;
     cp.max_smem = max_smem;
