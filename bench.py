@@ -40,10 +40,10 @@ KBAR, D, ALPHA = 30, 10, 1e-3
 WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
 L2_FLUSH_BYTES = 512 << 20
 GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused"}
-# DRAM bytes (read + write) of one k_dss_fused<128> launch in a warm ncu capture on star100k
-# (6.7 KB: the working set stays in L2 between the launches of an application), times the 30
+# DRAM bytes (read + write) of one k_dss_fused<256> launch in a warm ncu capture on star100k
+# (4.9 KB: the working set stays in L2 between the launches of an application), times the 30
 # launches of an application; reported only for that workload and schedule
-GNN_TRAFFIC = {("star100k", 3): 6656 * KBAR}
+GNN_TRAFFIC = {("star100k", 3): (1024 + 3840) * KBAR}
 
 
 def args_parse():
