@@ -25,7 +25,7 @@ namespace ddg {
 
 constexpr int KT = 256;            // threads per block of the vector kernels
 constexpr int RB = 1184;           // fixed grid of the streaming kernels: 8 CTAs of 256 on each of 148 SMs
-constexpr int MDG = 592;           // grid of the multi-dot and the direction update (4 CTAs of 256 per SM)
+constexpr int MDG = 296;           // grid of the multi-dot and the direction update (2 CTAs of 256 per SM)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
@@ -35,52 +35,17 @@ enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT
 enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
 
 // ------------------------------------------------------------------ SpMV
-// y_i = sum_e val[e] x[col[e]], one row per thread, a block per 256 consecutive rows.
-// The block first copies its rows' column indices and values (one contiguous range)
-// into shared memory with coalesced loads, then every thread sums its row from there
-// in CSR order (the same order, hence the same result, as a plain row loop).
-constexpr int SP_NNZ = 3072;  // shared-memory tile: up to 12 entries per row on average
-
-template <bool DOTS>
-__device__ __forceinline__ void spmv_tile(const int *__restrict__ rowptr, const int *__restrict__ col,
-                                          const double *__restrict__ val, const double *__restrict__ x,
-                                          double *__restrict__ y, int n, const double *__restrict__ r,
-                                          double &pq, double &pr) {
-    __shared__ int scol[SP_NNZ];
-    __shared__ double sval[SP_NNZ];
-    const int r0 = blockIdx.x * KT, r1 = min(n, r0 + KT);
-    const int i = r0 + threadIdx.x;
-    const int eb = rowptr[r0], ee = rowptr[r1];
-    const bool tiled = ee - eb <= SP_NNZ;  // uniform over the block
-    if (tiled) {
-        for (int e = eb + threadIdx.x; e < ee; e += KT) {
-            scol[e - eb] = col[e];
-            sval[e - eb] = val[e];
-        }
-    }
-    __syncthreads();
-    if (i < n) {
-        const int e0 = rowptr[i], e1 = rowptr[i + 1];
-        double acc = 0.0;
-        if (tiled) {
-            for (int e = e0 - eb; e < e1 - eb; ++e) acc += sval[e] * x[scol[e]];
-        } else {
-            for (int e = e0; e < e1; ++e) acc += val[e] * x[col[e]];
-        }
-        y[i] = acc;
-        if (DOTS) {
-            const double xi = x[i];
-            pq = xi * acc;
-            pr = xi * r[i];
-        }
-    }
-}
-
+// y_i = sum_e val[e] x[col[e]], one row per thread in CSR order.  (A shared-memory tiled form
+// and an eight-lanes-per-row form both measured slower: with ~7 nonzeros per row the L1 serves
+// the row-per-thread reuse, and the FP64 units bound these kernels on this part.)
 __global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
                                              const double *__restrict__ val, const double *__restrict__ x,
                                              double *__restrict__ y, int n) {
-    double pq = 0.0, pr = 0.0;
-    spmv_tile<false>(rowptr, col, val, x, y, n, nullptr, pq, pr);
+    const int i = blockIdx.x * KT + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * x[col[e]];
+    y[i] = acc;
 }
 
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
@@ -410,16 +375,24 @@ __global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, l
     }
 }
 
-// q = A p with the partial dots p.q and p.r (one row per thread, shared-memory tiles);
-// the last block forms alpha = (p.r) / (p.q)
+// q = A p with the partial dots p.q and p.r (one row per thread); the last block forms
+// alpha = (p.r) / (p.q)
 __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
                                                  const double *__restrict__ val, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
                                                  double *part, Window win, double *scal, int *flag) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
+    const int i = blockIdx.x * KT + threadIdx.x;
     double pq = 0.0, pr = 0.0;
-    spmv_tile<true>(rowptr, col, val, p, q, n, r, pq, pr);
+    if (i < n) {
+        double acc = 0.0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * p[col[e]];
+        q[i] = acc;
+        const double pi = p[i];
+        pq = pi * acc;
+        pr = pi * r[i];
+    }
     pq = block_sum(pq, sh);
     pr = block_sum(pr, sh);
     if (threadIdx.x == 0) {
