@@ -25,7 +25,8 @@ namespace ddg {
 
 constexpr int KT = 256;            // threads per block of the vector kernels
 constexpr int RB = 1184;           // fixed grid of the streaming kernels: 8 CTAs of 256 on each of 148 SMs
-constexpr int MDG = 296;           // grid of the multi-dot and the direction update (2 CTAs of 256 per SM)
+constexpr int MDG = 296;           // grid of the multi-dot (2 CTAs of 256 per SM)
+constexpr int PUG = 592;           // grid of the direction update (4 CTAs of 256 per SM)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
@@ -631,7 +632,7 @@ struct FcgRun {
             ++nl;
             DDG_LAUNCHES(1);
         }
-        k_pupdate<<<MDG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
+        k_pupdate<<<PUG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
         k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
         k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
         nl += 3;
