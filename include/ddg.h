@@ -271,7 +271,7 @@ int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max
 
 typedef struct ddg_solve_opts {
     int32_t kind;            /* DDG_DDM_GNN, DDG_DDM_LU or DDG_NONE */
-    uint32_t flags;          /* DDG_COARSE, DDG_POU_PROLONG */
+    uint32_t flags;          /* DDG_COARSE, DDG_POU_PROLONG, DDG_BF16_WEIGHTS */
     const ddg_model *model;  /* for DDG_DDM_GNN; must outlive the request */
     int32_t K;               /* subdomains; 0 = round(n_free / 1000) */
     int32_t overlap;         /* overlap layers */
@@ -293,8 +293,10 @@ typedef struct ddg_serve_summary {
  * the context admits queued requests in arrival order while fewer than
  * max_active run and their estimated device memory fits the context's HBM
  * budget, sets each up on a stream of its own and advances all running
- * solves a batch of iterations at a time, so their GPU work overlaps.
- * Thread-safe with ddg_poll and ddg_serve_stats. */
+ * solves a batch of iterations at a time, so their GPU work overlaps (or, with
+ * fused GNN launches, one iteration per step; see ddg_serve_config).
+ * Thread-safe with ddg_poll and ddg_serve_stats.  Errors: DDG_INVALID_ARG,
+ * DDG_BUSY (the admission queue holds max_pending requests). */
 int32_t ddg_submit(ddg_ctx *ctx, int32_t n_nodes, const double *xy, int32_t n_tri, const int32_t *tri,
                    const double r[9], const ddg_solve_opts *opts, uint64_t *ticket);
 /* DDG_PENDING while the request is queued or running; afterwards its final
