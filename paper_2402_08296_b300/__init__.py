@@ -120,6 +120,7 @@ _SIGS = {
     "ddg_serve_config": [_p, _i32, _i32, _i32],
     "ddg_serve_stats": [_p, ctypes.POINTER(ddg_serve_summary)],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
+    "ddg_fcg_history": [_p, _p, _i32, ctypes.POINTER(_i32)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -378,6 +379,16 @@ def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: 
     if st not in (DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN):
         raise DdgError(st, "ddg_fcg_solve")
     return rep.as_dict(), x
+
+
+def ddg_fcg_history(p) -> np.ndarray:
+    """|r| / |b| after every iteration of the problem's last ddg_fcg_solve."""
+    cnt = _i32()
+    _check(lib.ddg_fcg_history(p, None, 0, ctypes.byref(cnt)), "ddg_fcg_history")
+    out = np.zeros(cnt.value, np.float64)
+    if cnt.value:
+        _check(lib.ddg_fcg_history(p, out.ctypes.data_as(_p), cnt.value, ctypes.byref(cnt)), "ddg_fcg_history")
+    return out
 
 
 def ddg_submit(ctx, xy, tri, r, kind: int, model=None, flags: int = DDG_COARSE, K: int = 0, overlap: int = 2,

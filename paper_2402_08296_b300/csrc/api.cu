@@ -35,7 +35,7 @@ int32_t problem_create(ddg_ctx *c, int n_nodes, const double *xy, int n_tri, con
     p->own_stream = own_stream;
     p->n = n_nodes;
     p->t = n_tri;
-    for (ddg::Allocs *a : {&p->a_mesh, &p->a_matrix, &p->a_part, &p->a_pre, &p->a_kry, &p->chunk.allocs}) {
+    for (ddg::Allocs *a : {&p->a_mesh, &p->a_matrix, &p->a_part, &p->a_pre, &p->a_kry, &p->a_hist, &p->chunk.allocs}) {
         a->stream = stream;
         a->use_stream = true;
     }
@@ -134,6 +134,7 @@ int32_t ddg_problem_destroy(ddg_problem *p) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(p->stream);
     dfree_all(c, p->a_kry);
+    dfree_all(c, p->a_hist);
     dfree_all(c, p->a_pre);
     chunk_free(p);
     dfree_all(c, p->a_part);
@@ -395,6 +396,19 @@ int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, c
     for (int b = 0; b < nb; ++b) REQUIRE(graphs[b] >= 0 && graphs[b] < p->K, "graph index out of range");
     DDG_TRY(use_device(p->ctx));
     return train_loss_grad(p, m, r_dev, graphs, nb, loss, grad);
+}
+
+int32_t ddg_fcg_history(ddg_problem *p, double *rel_host, int32_t n, int32_t *count) {
+    API_BEGIN;
+    REQUIRE(p && count && n >= 0 && (rel_host || n == 0), "bad arguments");
+    DDG_TRY(use_device(p->ctx));
+    *count = p->khist_n;
+    const int m = std::min(n, p->khist_n);
+    if (m > 0) {
+        DDG_CU(cudaMemcpyAsync(rel_host, p->khist, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream));
+        DDG_CU(cudaStreamSynchronize(p->stream));
+    }
+    return DDG_OK;
 }
 
 int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,

@@ -199,6 +199,9 @@ struct ddg_problem {
     double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kP = nullptr, *kQ = nullptr, *kscal = nullptr;
     double *kpart = nullptr;   // block partials of reductions
     int *kflag = nullptr;
+    double *khist = nullptr;   // |r| / |b| after every iteration of the last solve
+    int khist_cap = 0, khist_n = 0;
+    ddg::Allocs a_hist;
     ddg::Allocs a_kry;
 };
 

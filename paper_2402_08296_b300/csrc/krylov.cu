@@ -418,7 +418,8 @@ __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr,
 
 // x += alpha p; r -= alpha q; the last block forms |r| / |b| and raises the stop flag
 __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p, const double *q, int n,
-                                           double *scal, double *part, int *flag, double tol) {
+                                           double *scal, double *part, int *flag, double tol, double *hist,
+                                           int hist_cap) {
     __shared__ double sh[32];
     if (flag[F_STOP]) return;
     double al = scal[S_ALPHA];
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p
         if (threadIdx.x == 0) {
             const double rel = sqrt(rr) / scal[S_BNORM];
             scal[S_REL] = rel;
+            if (hist && flag[F_ITERS] < hist_cap) hist[flag[F_ITERS]] = rel;
             flag[F_ITERS] += 1;
             if (!isfinite(rel)) flag[F_STOP] = 2;
             else if (rel < tol) flag[F_STOP] = 1;
@@ -555,6 +557,14 @@ struct FcgRun {
             DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
             p->kr_m = m;
         }
+        if (p->khist_cap < max_iter) {  // residual history of the solve (kept for ddg_fcg_history)
+            dfree_all(c, p->a_hist);
+            p->khist = nullptr;
+            p->khist_cap = 0;
+            DDG_TRY(dalloc(c, p->a_hist, &p->khist, (size_t)max_iter));
+            p->khist_cap = max_iter;
+        }
+        p->khist_n = 0;
         x = p->kx; r = p->kr; z = p->kz; P = p->kP; Q = p->kQ; scal = p->kscal; part = p->kpart;
         flag = p->kflag;
         ld = nf;
@@ -634,7 +644,7 @@ struct FcgRun {
         }
         k_pupdate<<<PUG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
         k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
-        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol);
+        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol, p->khist, p->khist_cap);
         nl += 3;
         DDG_LAUNCHES(3);
         return DDG_OK;
@@ -748,6 +758,7 @@ struct FcgRun {
         cudaEventElapsedTime(&ms, e0, e1);
         ddg_solve_report rp{};
         rp.iterations = hflag[F_ITERS];
+        p->khist_n = std::min(hflag[F_ITERS], p->khist_cap);
         rp.rel_residual = hs[S_REL];
         rp.true_rel_residual = htr / hs[S_BNORM];
         rp.solve_ms = ms;

@@ -192,3 +192,18 @@ def test_a_weight_copy_that_never_arrives_ends_in_a_timeout_status(ddg, ctx, mon
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)
 
+
+def test_residual_history_of_a_solve(ddg, ctx):
+    """ddg_fcg_history: one relative residual per iteration, ending at the report's value."""
+    w = synth.workload("square2k", 5)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE)
+        rep, _ = ddg.ddg_fcg_solve(p, 1e-8, 200, 10)
+        h = ddg.ddg_fcg_history(p)
+        assert rep["status"] == ddg.DDG_OK and len(h) == rep["iterations"]
+        assert h[-1] == rep["rel_residual"] and h[-1] < 1e-8 <= h[-2]
+        assert np.all(np.isfinite(h)) and h[0] < 1.0
+    finally:
+        ddg.ddg_problem_destroy(p)
+
