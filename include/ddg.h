@@ -260,8 +260,10 @@ int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, double *y_d
 /* Solve A_ff x = b_f by flexible CG (truncation m_trunc >= 1; m_trunc = 1
  * reproduces PCG for a fixed SPD preconditioner) from x0 (host, n_free, or
  * NULL = 0) until |r| / |b| < rtol or max_iter iterations.  x_host[n_nodes]
- * receives the full nodal solution (g on Dirichlet nodes).  Returns the
- * report's status: DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN, or DDG_TIMEOUT
+ * receives the full nodal solution (g on Dirichlet nodes).  Before the first
+ * iteration: b = 0 returns x = 0 (whatever x0) and a start vector with
+ * |b - A x0| / |b| < rtol returns x0, both with zero iterations and DDG_OK.
+ * Returns the report's status: DDG_OK, DDG_NOT_CONVERGED, DDG_BREAKDOWN, or DDG_TIMEOUT
  * when a kernel gave up a bounded wait during the solve (the context stays
  * usable). */
 int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max_iter, int32_t m_trunc,

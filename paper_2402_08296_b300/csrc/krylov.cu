@@ -32,7 +32,7 @@ constexpr int POLL = 4;            // iterations between stop-flag polls
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
 
 // scalar slots (kscal) and flags (kflag)
-enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT = 8 + 2 * MAXM };
+enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_R0 = 3, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT = 8 + 2 * MAXM };
 enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
 
 // ------------------------------------------------------------------ SpMV
@@ -446,6 +446,22 @@ __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p
     }
 }
 
+// Before the first iteration.  A zero right-hand side has the solution u = 0, so the
+// solve ends there with zero iterations (whatever the start vector); a start vector whose
+// residual already meets the tolerance ends it the same way.  Without this check both
+// cases would reach p.q = 0 in the first step and read as a breakdown.
+__global__ void k_initial_check(double *x, int n, double *scal, int *flag, double tol, int r0_is_b) {
+    const double bn = scal[S_BNORM];
+    if (bn == 0.0)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+            x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double rel = bn == 0.0 ? 0.0 : (r0_is_b ? 1.0 : scal[S_R0] / bn);
+        scal[S_REL] = rel;
+        if (bn == 0.0 || rel < tol) flag[F_STOP] = 1;
+    }
+}
+
 __global__ void k_sumsq_final(const double *part, int nb, double *out) {
     __shared__ double sh[32];
     double v = 0.0;
@@ -583,6 +599,13 @@ struct FcgRun {
             DDG_CU(cudaMemcpyAsync(r, p->b, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
         }
         DDG_TRY(norm2(p, p->b, scal + S_BNORM, s));
+        if (x0) {
+            DDG_TRY(norm2(p, r, scal + S_R0, s));
+            k_initial_check<<<RB, KT, 0, s>>>(x, nf, scal, flag, rtol, 0);
+        } else {
+            k_initial_check<<<1, 32, 0, s>>>(x, 0, scal, flag, rtol, 1);
+        }
+        DDG_LAUNCH_CHECK();
         DDG_CU(cudaEventCreate(&e0));
         DDG_CU(cudaEventCreate(&e1));
         DDG_CU(cudaEventCreateWithFlags(&batch_done, cudaEventDisableTiming));
@@ -760,7 +783,7 @@ struct FcgRun {
         rp.iterations = hflag[F_ITERS];
         p->khist_n = std::min(hflag[F_ITERS], p->khist_cap);
         rp.rel_residual = hs[S_REL];
-        rp.true_rel_residual = htr / hs[S_BNORM];
+        rp.true_rel_residual = hs[S_BNORM] > 0.0 ? htr / hs[S_BNORM] : 0.0;  // b = 0: u = 0 is exact
         rp.solve_ms = ms;
         rp.precond_ms = pre_ms;
         rp.local_ms = loc_ms;
