@@ -185,11 +185,24 @@ def run_ours(a, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     p = ddg.ddg_mesh_upload(ctx, w.mesh.xy, w.mesh.tri)
 
+    phase_names = ("assemble", "partition", "setup_precond", "fcg")
+    phases = {ddg.DDG_DDM_GNN: [], ddg.DDG_DDM_LU: []}
+
     def step(kind, problem, want_x=False):
+        # events on the library's stream between the calls: each phase's share of the step's
+        # device timeline (host gaps in which the GPU waits included)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
         ddg.ddg_assemble_poly(problem, w.coeffs)
+        ev[1].record(stream)
         ddg.ddg_partition(problem, w.K, w.overlap)
+        ev[2].record(stream)
         ddg.ddg_setup_precond(problem, kind, model if kind == ddg.DDG_DDM_GNN else None, ddg.DDG_COARSE)
-        return ddg.ddg_fcg_solve(problem, a.tol, a.max_iter, a.m, want_x=want_x)
+        ev[3].record(stream)
+        out = ddg.ddg_fcg_solve(problem, a.tol, a.max_iter, a.m, want_x=want_x)
+        ev[4].record(stream)
+        phases[kind].append(ev)
+        return out
 
     def timed(fn, n):
         """n steps, each bracketed by events on the library stream; L2 flushed between steps."""
@@ -220,6 +233,9 @@ def run_ours(a, rank, world, local_rank):
     for _ in range(a.warmup):
         step(ddg.DDG_DDM_GNN, p)
         step(ddg.DDG_DDM_LU, p)
+    torch.cuda.synchronize()
+    phases[ddg.DDG_DDM_GNN].clear()
+    phases[ddg.DDG_DDM_LU].clear()
     clocks = Clocks(local_rank)
     clocks.start()
     barrier()
@@ -271,6 +287,12 @@ def run_ours(a, rank, world, local_rank):
     local_ms = in_solve_ms
     local_launches = 1
 
+    def phase_ms(kind):
+        evs = phases[kind][:a.steps]   # the timed steps (the e2e steps come after them)
+        return {nm: float(np.median([e[i].elapsed_time(e[i + 1]) for e in evs]))
+                for i, nm in enumerate(phase_names)} if evs else {}
+
+    phases_gnn, phases_lu = phase_ms(ddg.DDG_DDM_GNN), phase_ms(ddg.DDG_DDM_LU)
     tot_gnn = max_over_ranks(float(t_gnn.sum()) / 1e3)
     tot_lu = max_over_ranks(float(t_lu.sum()) / 1e3)
     tot_e2e = max_over_ranks(float(t_e2e.sum()) / 1e3)
@@ -302,12 +324,13 @@ def run_ours(a, rank, world, local_rank):
         "converged": conv,
         "gnn": {"iterations": iters, "true_rel_residual": [r["true_rel_residual"] for r in r_gnn],
                 "p50_ms": float(np.percentile(t_gnn, 50)), "p99_ms": float(np.percentile(t_gnn, 99)),
-                "solve_ms": [r["solve_ms"] for r in r_gnn], "precond_ms": [r["precond_ms"] for r in r_gnn]},
+                "solve_ms": [r["solve_ms"] for r in r_gnn], "precond_ms": [r["precond_ms"] for r in r_gnn],
+                "phases_ms_p50": phases_gnn},
         "lu": {"value": replica_throughput(a.steps, world, tot_lu), "unit": "solves/s",
                "iterations": [r["iterations"] for r in r_lu],
                "true_rel_residual": [r["true_rel_residual"] for r in r_lu],
                "p50_ms": float(np.percentile(t_lu, 50)), "p99_ms": float(np.percentile(t_lu, 99)),
-               "solve_ms": [r["solve_ms"] for r in r_lu]},
+               "solve_ms": [r["solve_ms"] for r in r_lu], "phases_ms_p50": phases_lu},
         "e2e": {"value": replica_throughput(a.steps, world, tot_e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(w.mesh.xy.nbytes + w.mesh.t * 12 + 72),
                 "d2h_bytes_per_step": int(w.mesh.n * 8 + 64), "wall_s": wall_e2e,

@@ -24,8 +24,7 @@
 namespace ddg {
 
 constexpr int KT = 256;            // threads per block of the vector kernels
-constexpr int RB = 1184;           // fixed grid of the streaming kernels: 8 CTAs of 256 on each of 148 SMs
-constexpr int MDG = 296;           // grid of the multi-dot (2 CTAs of 256 per SM)
+constexpr int RB = 1184;           // grid of the norm kernels; bound on the reducing kernels' grids (partials per sum)
 constexpr int PUG = 592;           // grid of the direction update (4 CTAs of 256 per SM)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
@@ -34,6 +33,28 @@ constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, th
 // scalar slots (kscal) and flags (kflag)
 enum { S_BNORM = 0, S_ALPHA = 1, S_REL = 2, S_R0 = 3, S_BETA = 8, S_PQ = 8 + MAXM, S_COUNT = 8 + 2 * MAXM };
 enum { F_STOP = 0, F_ITERS = 1, F_T_MD = 2, F_T_SP = 3, F_T_XR = 4, F_COUNT = 5 };
+
+// Block sums of NV per-thread values, written to out[j * stride] for j < nv.  This part runs
+// FP64 at about 1/64 of its FP32 rate, so every FP64 instruction of a warp holds its
+// sub-partition's FP64 pipe for about 64 cycles, and a shuffle tree in every warp for every
+// sum (5 additions per warp and sum) costs more than the dot products themselves.  Instead
+// the values go through shared memory and warp j sums column j: KT/32 - 1 + 5 additions per
+// sum, in a fixed order.  sh holds nv * KT doubles.
+template <int NV>
+__device__ __forceinline__ void block_parts(const double (&v)[NV], int nv, double *sh, double *out, long long stride) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+        if (j < nv) sh[j * KT + threadIdx.x] = v[j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < nv; j += KT / 32) {
+        double t = sh[j * KT + lane];
+#pragma unroll
+        for (int k = 1; k < KT / 32; ++k) t += sh[j * KT + 32 * k + lane];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[j * stride] = t;
+    }
+}
 
 // ------------------------------------------------------------------ SpMV
 // y_i = sum_e val[e] x[col[e]], one row per thread in CSR order.  (A shared-memory tiled form
@@ -58,7 +79,8 @@ int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
 // ------------------------------------------------------------------ preconditioner pieces
 __global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *sub_idx, const double *inv_mult,
                                                  const double *r, double *s_out, double *y_out, const int *stop) {
-    __shared__ double sh[32];
+    __shared__ double sh[2 * KT];
+    __shared__ double tot[2];
     if (stop && *stop) return;
     int i = blockIdx.x;
     double ss = 0.0, yy = 0.0;
@@ -68,11 +90,12 @@ __global__ void __launch_bounds__(KT) k_restrict(const int *sub_ptr, const int *
         ss += v * v;
         yy += v * inv_mult[j];
     }
-    ss = block_sum(ss, sh);
-    yy = block_sum(yy, sh);
+    const double v[2] = {ss, yy};
+    block_parts<2>(v, 2, sh, tot, 1);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_out[i] = sqrt(ss);
-        y_out[i] = yy;
+        s_out[i] = sqrt(tot[0]);
+        y_out[i] = tot[1];
     }
 }
 
@@ -290,28 +313,6 @@ __device__ __forceinline__ bool last_block(int *ticket) {
     return is_last;
 }
 
-// sum of part[0..n) by the whole block in a fixed order (valid in thread 0); the loop is
-// unrolled so that a thread's loads are in flight together (the additions keep their order)
-__device__ __forceinline__ double block_sum_parts(const double *__restrict__ part, int n, double *sh) {
-    double v = 0.0;
-#pragma unroll 8
-    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
-    return block_sum(v, sh);
-}
-
-// the same for two interleaved sums of part[0..n) and part[n..2n)
-__device__ __forceinline__ void block_sum_parts2(const double *__restrict__ part, int n, double *sh, double &s0,
-                                                 double &s1) {
-    double v0 = 0.0, v1 = 0.0;
-#pragma unroll 8
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        v0 += part[b];
-        v1 += part[n + b];
-    }
-    s0 = block_sum(v0, sh);
-    s1 = block_sum(v1, sh);
-}
-
 // sum of part[0..n) by one warp in a fixed order (valid in every lane)
 __device__ __forceinline__ double warp_sum_parts(const double *__restrict__ part, int n, int lane) {
     double v = 0.0;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(KT) k_dot(const double *a, const double *b, in
 // d_j = z . Q[slot_j]; the last block forms beta_j = d_j / (p_j . q_j)
 __global__ void __launch_bounds__(KT, 4) k_multidot(const double *z, const double *Q, long long ld, Window win, int n,
                                                     double *part, double *scal, int *flag) {
-    __shared__ double sh[32];
+    __shared__ double sh[MAXM * KT];
     if (flag[F_STOP]) return;
     double acc[MAXM];
 #pragma unroll
@@ -343,13 +344,7 @@ __global__ void __launch_bounds__(KT, 4) k_multidot(const double *z, const doubl
         for (int j = 0; j < MAXM; ++j)
             if (j < win.W) acc[j] += zi * Q[win.slot[j] * ld + i];
     }
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {  // static indices keep acc[] in registers
-        if (j < win.W) {
-            double v = block_sum(acc[j], sh);
-            if (threadIdx.x == 0) part[j * RB + blockIdx.x] = v;
-        }
-    }
+    block_parts<MAXM>(acc, win.W, sh, part + blockIdx.x, RB);
     if (last_block(&flag[F_T_MD])) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int j = warp; j < win.W; j += KT / 32) {
@@ -376,34 +371,34 @@ __global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, l
     }
 }
 
-// q = A p with the partial dots p.q and p.r (one row per thread); the last block forms
-// alpha = (p.r) / (p.q)
+// q = A p with the partial dots p.q and p.r (rows strided over the grid, one row per thread
+// at a time); the last block forms alpha = (p.r) / (p.q)
 __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
                                                  const double *__restrict__ val, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
                                                  double *part, Window win, double *scal, int *flag) {
-    __shared__ double sh[32];
+    __shared__ double sh[2 * KT];
+    __shared__ double tot[2];
     if (flag[F_STOP]) return;
-    const int i = blockIdx.x * KT + threadIdx.x;
-    double pq = 0.0, pr = 0.0;
-    if (i < n) {
+    double d[2] = {0.0, 0.0};  // p.q, p.r
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
         double acc = 0.0;
         for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * p[col[e]];
         q[i] = acc;
         const double pi = p[i];
-        pq = pi * acc;
-        pr = pi * r[i];
+        d[0] += pi * acc;
+        d[1] += pi * r[i];
     }
-    pq = block_sum(pq, sh);
-    pr = block_sum(pr, sh);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = pq;
-        part[gridDim.x + blockIdx.x] = pr;
-    }
+    block_parts<2>(d, 2, sh, part + blockIdx.x, gridDim.x);
     if (last_block(&flag[F_T_SP])) {
-        double spq, spr;
-        block_sum_parts2(part, gridDim.x, sh, spq, spr);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (warp < 2) {
+            const double t = warp_sum_parts(part + warp * gridDim.x, gridDim.x, lane);
+            if (lane == 0) tot[warp] = t;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
+            const double spq = tot[0], spr = tot[1];
             const double al = spr / spq;
             if (!(spq > 0.0) || !isfinite(al)) {
                 flag[F_STOP] = 2;
@@ -420,20 +415,19 @@ __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr,
 __global__ void __launch_bounds__(KT) k_xr(double *x, double *r, const double *p, const double *q, int n,
                                            double *scal, double *part, int *flag, double tol, double *hist,
                                            int hist_cap) {
-    __shared__ double sh[32];
+    __shared__ double sh[KT];
     if (flag[F_STOP]) return;
     double al = scal[S_ALPHA];
-    double v = 0.0;
-    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)RB * KT) {
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
         x[i] += al * p[i];
         double ri = r[i] - al * q[i];
         r[i] = ri;
-        v += ri * ri;
+        v[0] += ri * ri;
     }
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-    if (last_block(&flag[F_T_XR])) {
-        const double rr = block_sum_parts(part, RB, sh);
+    block_parts<1>(v, 1, sh, part + blockIdx.x, 0);
+    if (last_block(&flag[F_T_XR]) && threadIdx.x < 32) {
+        const double rr = warp_sum_parts(part, gridDim.x, threadIdx.x);
         if (threadIdx.x == 0) {
             const double rel = sqrt(rr) / scal[S_BNORM];
             scal[S_REL] = rel;
@@ -502,6 +496,7 @@ struct FcgRun {
     cudaStream_t s = nullptr;
     double rtol = 0.0;
     int max_iter = 0, m = 0, nf = 0, L = 0, nb_spmv = 0;
+    int G = 1;  // grid of the reducing FCG kernels (multi-dot, SpMV with its dots, x/r update)
     long long ld = 0, off_sp = 0, off_rr = 0;
     double *record = nullptr;
     double *x = nullptr, *r = nullptr, *z = nullptr, *P = nullptr, *Q = nullptr, *scal = nullptr, *part = nullptr;
@@ -612,7 +607,15 @@ struct FcgRun {
         L = m * ((POLL + m - 1) / m);  // iterations per captured period: a multiple of m, at least POLL
         ev.resize(4 * std::max(POLL, L));
         for (auto &e : ev) DDG_CU(cudaEventCreate(&e));
-        nb_spmv = cdiv(nf, KT);
+        {
+            // between one and two CTAs per SM, so that a thread takes several rows and the block
+            // sums (FP64) stay a small share; no more CTAs than row blocks
+            int sms = 148;
+            DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+            long long g = std::min(std::max((long long)cdiv(nf, KT * 8), (long long)sms), 2LL * sms);
+            G = (int)std::max(1LL, std::min(g, (long long)cdiv(nf, KT)));
+        }
+        nb_spmv = G;
         off_sp = OFF_MD + MAXM * RB;
         off_rr = off_sp + 2LL * nb_spmv;
         use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;
@@ -661,13 +664,13 @@ struct FcgRun {
     int32_t fcg_kernels(const Window &win, int &nl) {
         double *pn = P + win.snew * ld, *qn = Q + win.snew * ld;
         if (win.W > 0) {
-            k_multidot<<<MDG, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
+            k_multidot<<<G, KT, 0, s>>>(z, Q, ld, win, nf, part + OFF_MD, scal, flag);
             ++nl;
             DDG_LAUNCHES(1);
         }
         k_pupdate<<<PUG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
         k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
-        k_xr<<<RB, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol, p->khist, p->khist_cap);
+        k_xr<<<G, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol, p->khist, p->khist_cap);
         nl += 3;
         DDG_LAUNCHES(3);
         return DDG_OK;
@@ -698,29 +701,37 @@ struct FcgRun {
     // The first m iterations grow the direction window; from iteration m on the
     // ring slots repeat with period m, so one period is captured as a CUDA graph
     // and replayed.  Queues one batch and the copy of the stop flag behind it.
+    // Captures one period of L iterations (ring windows of iterations m .. m + L - 1, the same for
+    // every period that starts at a multiple of m) and instantiates it.  The launches recorded
+    // during the capture are not executions: they are taken back out of the counters, and every
+    // replay adds them.
+    int32_t capture_period() {
+        const int l0 = launches, ll0 = loc_launches, la0 = loc_applies;
+        const unsigned long long g0 = launch_count();
+        DDG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int32_t st = DDG_OK;
+        for (int q = 0; q < L && st == DDG_OK; ++q) st = launch_iter(m + q, q);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != DDG_OK) return st;
+        DDG_CU(ce);
+        DDG_CU(cudaGraphInstantiate(&gexec, graph, 0));
+        per_launches = launches - l0;
+        per_loc_launches = loc_launches - ll0;
+        per_loc_applies = loc_applies - la0;
+        per_global = (int)(launch_count() - g0);
+        launches = l0;
+        loc_launches = ll0;
+        loc_applies = la0;
+        note_launches(-per_global);
+        return DDG_OK;
+    }
+
     int32_t launch_batch() {
-        if (use_graph && it >= m && it % m == 0 && max_iter - it >= L) {
-            if (!gexec) {
-                // the capture counts the period's launches once; every later replay adds them again
-                const int l0 = launches, ll0 = loc_launches, la0 = loc_applies;
-                const unsigned long long g0 = launch_count();
-                DDG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                int32_t st = DDG_OK;
-                for (int q = 0; q < L && st == DDG_OK; ++q) st = launch_iter(it + q, q);
-                cudaError_t ce = cudaStreamEndCapture(s, &graph);
-                if (st != DDG_OK) return st;
-                DDG_CU(ce);
-                DDG_CU(cudaGraphInstantiate(&gexec, graph, 0));
-                per_launches = launches - l0;
-                per_loc_launches = loc_launches - ll0;
-                per_loc_applies = loc_applies - la0;
-                per_global = (int)(launch_count() - g0);
-            } else {
-                launches += per_launches;
-                loc_launches += per_loc_launches;
-                loc_applies += per_loc_applies;
-                note_launches(per_global);
-            }
+        if (gexec && it >= m && it % m == 0 && max_iter - it >= L) {
+            launches += per_launches;
+            loc_launches += per_loc_launches;
+            loc_applies += per_loc_applies;
+            note_launches(per_global);
             DDG_CU(cudaGraphLaunch(gexec, s));
             it += L;
             in_flight = L;
@@ -735,6 +746,9 @@ struct FcgRun {
         }
         DDG_CU(cudaMemcpyAsync(hflag, flag, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, s));
         DDG_CU(cudaEventRecord(batch_done, s));
+        // with this batch queued, the host captures the replayed period while the GPU works on
+        // it, instead of leaving the GPU idle for the capture when iteration m is reached
+        if (use_graph && !gexec && max_iter - m >= L) DDG_TRY(capture_period());
         return DDG_OK;
     }
 
