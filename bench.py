@@ -552,7 +552,9 @@ def oracle_sample(a, budget_s: float):
         t_setup = time.perf_counter() - t0
         r = P.b
         done, t_dss = 0, 0.0
-        while done < len(Dd.sets) and t_setup + t_dss < budget_s:
+        # at least one round of subdomains, even when assembly and decomposition of a large mesh
+        # alone use up the budget
+        while done < len(Dd.sets) and (done == 0 or t_setup + t_dss < budget_s):
             jobs = []
             for S in Dd.sets[done: done + cores]:
                 t1 = time.perf_counter()
