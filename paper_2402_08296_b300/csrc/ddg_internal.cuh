@@ -215,6 +215,38 @@ int32_t dalloc(ddg_ctx *ctx, Allocs &a, T **p, size_t n) {
 }
 void dfree_all(ddg_ctx *ctx, Allocs &a);
 
+// Stream-ordered temporaries of one host scope.  Every pointer taken with get() is freed on
+// the stream when the scope ends, on every return path (the early returns of DDG_TRY and
+// DDG_CU included); drop() frees one earlier.  A pointer taken here is never passed to
+// cudaFreeAsync directly.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch() {
+        for (void *q : ptrs_) cudaFreeAsync(q, s_);
+    }
+    template <class T>
+    cudaError_t get(T **p, size_t n) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(p), sizeof(T) * n, s_);
+        if (e == cudaSuccess) ptrs_.push_back(*p);
+        return e;
+    }
+    cudaError_t drop(void *q) {
+        for (size_t i = 0; i < ptrs_.size(); ++i)
+            if (ptrs_[i] == q) {
+                ptrs_.erase(ptrs_.begin() + (long)i);
+                return cudaFreeAsync(q, s_);
+            }
+        return cudaSuccess;
+    }
+
+  private:
+    cudaStream_t s_;
+    std::vector<void *> ptrs_;
+};
+
 int32_t check_status(ddg_problem *p, const char *where);
 const char *last_error_cstr();
 int32_t problem_create(ddg_ctx *c, int n_nodes, const double *xy, int n_tri, const int *tri, const uint8_t *dirichlet,

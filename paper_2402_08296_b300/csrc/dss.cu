@@ -1403,8 +1403,9 @@ int32_t chunk_build(ddg_problem *p, int T) {
     DDG_CU(cudaMemcpyAsync(cp.c_graph, cg.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    Scratch sc(s);
     int *adj_n = nullptr;
-    DDG_CU(cudaMallocAsync(&adj_n, sizeof(int) * nc, s));
+    DDG_CU(sc.get(&adj_n, nc));
     k_chunk_build<<<nc, CH_T, 0, s>>>(cp.c_graph, cp.c_n0, cp.c_own, p->loc_ptr, p->nbr_ptr, p->nbr_off, p->nbr, 0,
                                       cp.c_need_n, adj_n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                       p->d_status);
@@ -1437,7 +1438,7 @@ int32_t chunk_build(ddg_problem *p, int T) {
                                       nullptr, nullptr, cp.c_need_off, cp.need, cp.c_adj_off, cp.adj_ptr,
                                       cp.c_adj_base, cp.adj, p->d_status);
     DDG_LAUNCH_CHECK();
-    DDG_CU(cudaFreeAsync(adj_n, s));
+    DDG_CU(sc.drop(adj_n));
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
 }
@@ -1550,8 +1551,9 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     DDG_CU(cudaMemcpyAsync(cp.gid, gid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    Scratch sc(s);
     int *adj_n = nullptr;
-    DDG_CU(cudaMallocAsync(&adj_n, sizeof(int) * nc, s));
+    DDG_CU(sc.get(&adj_n, nc));
     k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
                                       p->nbr, p->sub_ptr, p->sub_idx, 0, cp.c_need_n, adj_n, nullptr, nullptr,
                                       nullptr, nullptr, nullptr, nullptr, nullptr, p->d_status);
@@ -1591,7 +1593,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
                                       p->nbr, p->sub_ptr, p->sub_idx, 1, nullptr, nullptr, cp.c_need_off, cp.need,
                                       cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->d_status);
     DDG_LAUNCH_CHECK();
-    DDG_CU(cudaFreeAsync(adj_n, s));
+    DDG_CU(sc.drop(adj_n));
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
 }

@@ -131,12 +131,13 @@ int32_t mesh_build(ddg_problem *p, const uint8_t *dirichlet_host) {
     ddg_ctx *c = p->ctx;
     cudaStream_t s = p->stream;
     const int n = p->n, t = p->t;
+    Scratch sc(s);
     int *cnt = nullptr, *fill = nullptr, *deg = nullptr;
     uint8_t *bnd = nullptr;
-    DDG_CU(cudaMallocAsync(&cnt, sizeof(int) * (n + 1), s));
-    DDG_CU(cudaMallocAsync(&fill, sizeof(int) * (n + 1), s));
-    DDG_CU(cudaMallocAsync(&deg, sizeof(int) * (n + 1), s));
-    DDG_CU(cudaMallocAsync(&bnd, n, s));
+    DDG_CU(sc.get(&cnt, n + 1));
+    DDG_CU(sc.get(&fill, n + 1));
+    DDG_CU(sc.get(&deg, n + 1));
+    DDG_CU(sc.get(&bnd, n));
     DDG_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s));
     DDG_CU(cudaMemsetAsync(fill, 0, sizeof(int) * (n + 1), s));
 
@@ -173,8 +174,8 @@ int32_t mesh_build(ddg_problem *p, const uint8_t *dirichlet_host) {
 
     // h_bar
     double *len = nullptr, *sum = nullptr;
-    DDG_CU(cudaMallocAsync(&len, sizeof(double) * n, s));
-    DDG_CU(cudaMallocAsync(&sum, sizeof(double), s));
+    DDG_CU(sc.get(&len, n));
+    DDG_CU(sc.get(&sum, 1));
     k_edge_len<<<cdiv(n, 256), 256, 0, s>>>(p->xy, p->adj_ptr, p->adj_idx, n, len);
     DDG_LAUNCH_CHECK();
     DDG_TRY(reduce_sum(c, len, n, sum, s));
@@ -198,12 +199,6 @@ int32_t mesh_build(ddg_problem *p, const uint8_t *dirichlet_host) {
     k_free_ids<<<cdiv(n, 256), 256, 0, s>>>(p->dir, p->xy, n, p->free_id, p->free_node, p->xy_free);
     DDG_LAUNCH_CHECK();
 
-    DDG_CU(cudaFreeAsync(cnt, s));
-    DDG_CU(cudaFreeAsync(fill, s));
-    DDG_CU(cudaFreeAsync(deg, s));
-    DDG_CU(cudaFreeAsync(bnd, s));
-    DDG_CU(cudaFreeAsync(len, s));
-    DDG_CU(cudaFreeAsync(sum, s));
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "mesh upload");
 }
@@ -332,10 +327,11 @@ int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal_host, c
     const int n = p->n, nf = p->nf;
     Poly q{};
     if (r9) for (int k = 0; k < 9; ++k) q.r[k] = r9[k];
+    Scratch sc(s);
     double *fn = nullptr, *gn = nullptr;
     if (f_nodal_host) {
-        DDG_CU(cudaMallocAsync(&fn, sizeof(double) * n, s));
-        DDG_CU(cudaMallocAsync(&gn, sizeof(double) * n, s));
+        DDG_CU(sc.get(&fn, n));
+        DDG_CU(sc.get(&gn, n));
         DDG_CU(cudaMemcpyAsync(fn, f_nodal_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         DDG_CU(cudaMemcpyAsync(gn, g_nodal_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     }
@@ -356,10 +352,6 @@ int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal_host, c
                                              p->dir, p->free_id, p->free_node, p->g, nf, q, fn, p->rowptr,
                                              p->col, p->val, p->b);
     DDG_LAUNCH_CHECK();
-    if (fn) {
-        DDG_CU(cudaFreeAsync(fn, s));
-        DDG_CU(cudaFreeAsync(gn, s));
-    }
     DDG_CU(cudaStreamSynchronize(s));
     p->assembled = true;
     return check_status(p, "assemble");

@@ -94,16 +94,17 @@ static int32_t rcb(ddg_problem *p, int K) {
     ddg_ctx *c = p->ctx;
     cudaStream_t s = p->stream;
     const int nf = p->nf;
+    Scratch sc(s);
     int *Lx, *Ly, *Ln, *flag, *scan;
     uint8_t *side;
     int *dseg;  // 6 arrays of K ints: start, len, K, base, axis, n1
-    DDG_CU(cudaMallocAsync(&Lx, sizeof(int) * nf, s));
-    DDG_CU(cudaMallocAsync(&Ly, sizeof(int) * nf, s));
-    DDG_CU(cudaMallocAsync(&Ln, sizeof(int) * nf, s));
-    DDG_CU(cudaMallocAsync(&flag, sizeof(int) * (nf + 1), s));
-    DDG_CU(cudaMallocAsync(&scan, sizeof(int) * (nf + 1), s));
-    DDG_CU(cudaMallocAsync(&side, nf, s));
-    DDG_CU(cudaMallocAsync(&dseg, sizeof(int) * 6 * K, s));
+    DDG_CU(sc.get(&Lx, nf));
+    DDG_CU(sc.get(&Ly, nf));
+    DDG_CU(sc.get(&Ln, nf));
+    DDG_CU(sc.get(&flag, nf + 1));
+    DDG_CU(sc.get(&scan, nf + 1));
+    DDG_CU(sc.get(&side, nf));
+    DDG_CU(sc.get(&dseg, 6LL * K));
     DDG_TRY(sort_points(c, p->xy_free, nf, 0, Lx, s));
     DDG_TRY(sort_points(c, p->xy_free, nf, 1, Ly, s));
     std::vector<int> st{0}, len{nf}, kk{K}, base{0};
@@ -159,8 +160,6 @@ static int32_t rcb(ddg_problem *p, int K) {
     DDG_CU(cudaMemcpyAsync(d_base, base.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
     k_part_from_segments<<<cdiv(nf, 256), 256, 0, s>>>(Lx, nf, d_st, ns, d_base, p->part);
     DDG_LAUNCH_CHECK();
-    for (void *q : {(void *)Lx, (void *)Ly, (void *)Ln, (void *)flag, (void *)scan, (void *)side, (void *)dseg})
-        DDG_CU(cudaFreeAsync(q, s));
     return DDG_OK;
 }
 
@@ -560,17 +559,18 @@ int32_t coarse_build(ddg_problem *p) {
     DDG_LAUNCH_CHECK();
     DDG_TRY(check_status(p, "coarse matrix"));
     DDG_CU(cudaMemcpyAsync(p->A0inv, p->A0, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+    Scratch sc(s);
     double *prow, *fcol;
-    DDG_CU(cudaMallocAsync(&prow, sizeof(double) * K, s));
-    DDG_CU(cudaMallocAsync(&fcol, sizeof(double) * K, s));
+    DDG_CU(sc.get(&prow, K));
+    DDG_CU(sc.get(&fcol, K));
     long long KK = (long long)K * K;
     for (int k = 0; k < K; ++k) {
         k_gj_pivot<<<cdiv(K, 256), 256, 0, s>>>(p->A0inv, K, k, prow, fcol, p->d_status);
         k_gj_update<<<cdiv(KK, 256), 256, 0, s>>>(p->A0inv, K, k, prow, fcol);
     }
     DDG_LAUNCHES(2 * K);
-    DDG_CU(cudaFreeAsync(prow, s));
-    DDG_CU(cudaFreeAsync(fcol, s));
+    DDG_CU(sc.drop(prow));
+    DDG_CU(sc.drop(fcol));
     DDG_CU(cudaStreamSynchronize(s));
     int32_t r = check_status(p, "coarse inverse");
     if (r == DDG_INVALID_ARG) set_error("coarse matrix A_0 is not positive definite");
@@ -603,6 +603,7 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     p->kind = DDG_NONE;
     p->K = 0;
     const int nf = p->nf;
+    Scratch sc(s);
     DDG_TRY(dalloc(c, p->a_part, &p->part, nf));
     if (part_host) {
         DDG_CU(cudaMemcpyAsync(p->part, part_host, sizeof(int) * nf, cudaMemcpyHostToDevice, s));
@@ -610,7 +611,7 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
         DDG_TRY(rcb(p, K));
     }
     int *cnt;
-    DDG_CU(cudaMallocAsync(&cnt, sizeof(int) * (std::max(nf, K) + 1), s));
+    DDG_CU(sc.get(&cnt, std::max(nf, K) + 1));
     DDG_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * K, s));
     k_check_part<<<cdiv(nf, 256), 256, 0, s>>>(p->part, nf, K, p->d_status, cnt);
     DDG_LAUNCH_CHECK();
@@ -627,26 +628,26 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     }
     // membership sets, grown layer by layer
     int *mptr, *midx;
-    DDG_CU(cudaMallocAsync(&mptr, sizeof(int) * (nf + 1), s));
-    DDG_CU(cudaMallocAsync(&midx, sizeof(int) * nf, s));
+    DDG_CU(sc.get(&mptr, nf + 1));
+    DDG_CU(sc.get(&midx, nf));
     k_mem_init<<<cdiv(nf + 1, 256), 256, 0, s>>>(p->part, nf, mptr, midx);
     DDG_LAUNCH_CHECK();
     int total = nf;
     for (int layer = 0; layer < delta; ++layer) {
         int *nptr, *nidx;
-        DDG_CU(cudaMallocAsync(&nptr, sizeof(int) * (nf + 1), s));
+        DDG_CU(sc.get(&nptr, nf + 1));
         k_mem_layer<<<cdiv(nf, 128), 128, 0, s>>>(p->rowptr, p->col, mptr, midx, nf, 0, nptr, nullptr, nullptr,
                                                   p->d_status);
         DDG_LAUNCH_CHECK();
         DDG_TRY(check_status(p, "overlap"));
         DDG_CU(cudaMemsetAsync(nptr + nf, 0, sizeof(int), s));
         DDG_TRY(scan_exclusive(c, nptr, nptr, nf + 1, &total, s));
-        DDG_CU(cudaMallocAsync(&nidx, sizeof(int) * total, s));
+        DDG_CU(sc.get(&nidx, total));
         k_mem_layer<<<cdiv(nf, 128), 128, 0, s>>>(p->rowptr, p->col, mptr, midx, nf, 1, nullptr, nptr, nidx,
                                                   p->d_status);
         DDG_LAUNCH_CHECK();
-        DDG_CU(cudaFreeAsync(mptr, s));
-        DDG_CU(cudaFreeAsync(midx, s));
+        DDG_CU(sc.drop(mptr));
+        DDG_CU(sc.drop(midx));
         mptr = nptr;
         midx = nidx;
     }
@@ -654,15 +655,15 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     DDG_TRY(dalloc(c, p->a_part, &p->mem_idx, total));
     DDG_CU(cudaMemcpyAsync(p->mem_ptr, mptr, sizeof(int) * (nf + 1), cudaMemcpyDeviceToDevice, s));
     DDG_CU(cudaMemcpyAsync(p->mem_idx, midx, sizeof(int) * total, cudaMemcpyDeviceToDevice, s));
-    DDG_CU(cudaFreeAsync(mptr, s));
-    DDG_CU(cudaFreeAsync(midx, s));
+    DDG_CU(sc.drop(mptr));
+    DDG_CU(sc.drop(midx));
     p->sum_k = total;
 
     // subdomain lists: pairs (node, sub) sorted by (sub, node)
     int *pnode, *psub, *order;
-    DDG_CU(cudaMallocAsync(&pnode, sizeof(int) * total, s));
-    DDG_CU(cudaMallocAsync(&psub, sizeof(int) * total, s));
-    DDG_CU(cudaMallocAsync(&order, sizeof(int) * total, s));
+    DDG_CU(sc.get(&pnode, total));
+    DDG_CU(sc.get(&psub, total));
+    DDG_CU(sc.get(&order, total));
     DDG_TRY(dalloc(c, p->a_part, &p->mult, nf));
     DDG_TRY(dalloc(c, p->a_part, &p->inv_mult, nf));
     k_pairs<<<cdiv(nf, 256), 256, 0, s>>>(p->mem_ptr, p->mem_idx, nf, pnode, psub, p->mult, p->inv_mult);
@@ -675,16 +676,16 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     k_sub_lists<<<cdiv(total, 256), 256, 0, s>>>(order, pnode, psub, total, p->sub_idx, p->inv_pos, p->sub_ptr);
     DDG_LAUNCH_CHECK();
     DDG_TRY(scan_exclusive(c, p->sub_ptr, p->sub_ptr, K + 1, nullptr, s));
-    DDG_CU(cudaFreeAsync(pnode, s));
-    DDG_CU(cudaFreeAsync(psub, s));
-    DDG_CU(cudaFreeAsync(order, s));
+    DDG_CU(sc.drop(pnode));
+    DDG_CU(sc.drop(psub));
+    DDG_CU(sc.drop(order));
     p->K = K;
     p->delta = delta;
 
     // local graphs
     int *n_loc, *n_edge;
-    DDG_CU(cudaMallocAsync(&n_loc, sizeof(int) * (K + 1), s));
-    DDG_CU(cudaMallocAsync(&n_edge, sizeof(int) * (K + 1), s));
+    DDG_CU(sc.get(&n_loc, K + 1));
+    DDG_CU(sc.get(&n_edge, K + 1));
     k_graph_count<<<K, LG_T, 0, s>>>(p->sub_ptr, p->sub_idx, p->free_node, p->adj_ptr, p->adj_idx, p->dir,
                                       p->free_id, p->mem_ptr, p->mem_idx, n_loc, n_edge, p->d_status);
     DDG_LAUNCH_CHECK();
@@ -717,19 +718,19 @@ int32_t partition_build(ddg_problem *p, int K, int delta, const int *part_host) 
     DDG_LAUNCH_CHECK();
     // largest graphs first (the block scheduler then hands them out greedily)
     int *neg, *ids;
-    DDG_CU(cudaMallocAsync(&neg, sizeof(int) * K, s));
-    DDG_CU(cudaMallocAsync(&ids, sizeof(int) * K, s));
+    DDG_CU(sc.get(&neg, K));
+    DDG_CU(sc.get(&ids, K));
     DDG_TRY(dalloc(c, p->a_part, &p->lpt_order, K));
     k_diff<<<cdiv(K, 256), 256, 0, s>>>(p->loc_ptr, K, neg);
     k_neg<<<cdiv(K, 256), 256, 0, s>>>(neg, K, neg);
     k_iota_i<<<cdiv(K, 256), 256, 0, s>>>(ids, K);
     DDG_LAUNCHES(3);
     DDG_TRY(sort_pairs(c, neg, ids, K, p->lpt_order, s));
-    DDG_CU(cudaFreeAsync(neg, s));
-    DDG_CU(cudaFreeAsync(ids, s));
-    DDG_CU(cudaFreeAsync(n_loc, s));
-    DDG_CU(cudaFreeAsync(n_edge, s));
-    DDG_CU(cudaFreeAsync(cnt, s));
+    DDG_CU(sc.drop(neg));
+    DDG_CU(sc.drop(ids));
+    DDG_CU(sc.drop(n_loc));
+    DDG_CU(sc.drop(n_edge));
+    DDG_CU(sc.drop(cnt));
     DDG_TRY(check_status(p, "local graphs"));
     return coarse_build(p);
 }

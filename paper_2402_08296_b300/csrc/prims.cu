@@ -116,27 +116,27 @@ __global__ void k_scan_add(int *out, const int *offs, int n) {
 // exclusive scan of n ints; in == out allowed; total_host (if not NULL) receives the sum
 static int32_t scan_rec(const int *in, int *out, int n, int *total_dev, cudaStream_t s) {
     int nb = cdiv(n, SCAN_TILE);
+    Scratch sc(s);
     int *sums = nullptr, *offs = nullptr;
-    DDG_CU(cudaMallocAsync(&sums, sizeof(int) * (nb + 1), s));
+    DDG_CU(sc.get(&sums, nb + 1));
     k_scan_tile<<<nb, SCAN_T, 0, s>>>(in, out, sums, n);
     DDG_LAUNCH_CHECK();
     if (nb == 1) {
         DDG_CU(cudaMemcpyAsync(total_dev, sums, sizeof(int), cudaMemcpyDeviceToDevice, s));
     } else {
-        DDG_CU(cudaMallocAsync(&offs, sizeof(int) * nb, s));
+        DDG_CU(sc.get(&offs, nb));
         DDG_TRY(scan_rec(sums, offs, nb, total_dev, s));
         k_scan_add<<<cdiv(n, 256), 256, 0, s>>>(out, offs, n);
         DDG_LAUNCH_CHECK();
-        DDG_CU(cudaFreeAsync(offs, s));
     }
-    DDG_CU(cudaFreeAsync(sums, s));
     return DDG_OK;
 }
 
 int32_t scan_exclusive(ddg_ctx *ctx, const int *in, int *out, int n, int *total_host, cudaStream_t s) {
     (void)ctx;
+    Scratch sc(s);
     int *tot = nullptr;
-    DDG_CU(cudaMallocAsync(&tot, sizeof(int), s));
+    DDG_CU(sc.get(&tot, 1));
     if (n == 0) {
         DDG_CU(cudaMemsetAsync(tot, 0, sizeof(int), s));
     } else {
@@ -146,7 +146,6 @@ int32_t scan_exclusive(ddg_ctx *ctx, const int *in, int *out, int n, int *total_
         DDG_CU(cudaMemcpyAsync(total_host, tot, sizeof(int), cudaMemcpyDeviceToHost, s));
         DDG_CU(cudaStreamSynchronize(s));
     }
-    DDG_CU(cudaFreeAsync(tot, s));
     return DDG_OK;
 }
 
@@ -183,8 +182,9 @@ __global__ void k_iota(int *a, int n) {
 template <class Cmp>
 static int32_t merge_sort(int *idx, int n, Cmp cmp, cudaStream_t s) {
     if (n <= 1) return DDG_OK;
+    Scratch sc(s);
     int *tmp = nullptr;
-    DDG_CU(cudaMallocAsync(&tmp, sizeof(int) * n, s));
+    DDG_CU(sc.get(&tmp, n));
     int *a = idx, *b = tmp;
     for (long long w = 1; w < n; w *= 2) {
         k_merge_pass<<<cdiv(n, 256), 256, 0, s>>>(a, b, n, (int)w, cmp);
@@ -192,7 +192,6 @@ static int32_t merge_sort(int *idx, int n, Cmp cmp, cudaStream_t s) {
         int *t = a; a = b; b = t;
     }
     if (a != idx) DDG_CU(cudaMemcpyAsync(idx, a, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
-    DDG_CU(cudaFreeAsync(tmp, s));
     return DDG_OK;
 }
 
@@ -256,13 +255,13 @@ __global__ void __launch_bounds__(RED_T) k_sum_final(const double *part, int np,
 
 int32_t reduce_sum(ddg_ctx *ctx, const double *in, int n, double *out_dev, cudaStream_t s) {
     (void)ctx;
+    Scratch sc(s);
     double *part = nullptr;
-    DDG_CU(cudaMallocAsync(&part, sizeof(double) * RED_BLOCKS, s));
+    DDG_CU(sc.get(&part, RED_BLOCKS));
     k_sum_partial<<<RED_BLOCKS, RED_T, 0, s>>>(in, n, part);
     DDG_LAUNCH_CHECK();
     k_sum_final<<<1, RED_T, 0, s>>>(part, RED_BLOCKS, out_dev);
     DDG_LAUNCH_CHECK();
-    DDG_CU(cudaFreeAsync(part, s));
     return DDG_OK;
 }
 
