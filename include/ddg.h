@@ -12,7 +12,9 @@
  * Conventions
  *  - Every call returns an int32_t status (DDG_OK = 0 or a negative code).
  *    No call aborts, throws or traps; after a failure ddg_last_error()
- *    returns a message for the calling thread.
+ *    returns a message for the calling thread.  Besides the codes listed
+ *    with each call, any call may return DDG_OOM when host memory runs out
+ *    and DDG_INTERNAL for another host-side failure.
  *  - Handles are opaque and owned by the caller, who frees them with the
  *    matching *_destroy call.  A problem or model must be destroyed before
  *    its context.
@@ -54,7 +56,8 @@ enum ddg_status {
     DDG_TIMEOUT = -7,       /* a kernel's bounded wait (about one second) ran out; the context stays usable */
     DDG_PENDING = -8,       /* ddg_poll: the request has not finished yet */
     DDG_BAD_MESH = -9,      /* degenerate or inverted triangle, or a node of too high degree */
-    DDG_TOO_LARGE = -10     /* a subdomain or node list beyond a kernel's on-chip capacity */
+    DDG_TOO_LARGE = -10,    /* a subdomain or node list beyond a kernel's on-chip capacity */
+    DDG_INTERNAL = -11      /* a host-side failure other than memory (a thread that cannot be started) */
 };
 
 enum ddg_precond_kind { DDG_NONE = 0, DDG_DDM_LU = 1, DDG_DDM_GNN = 2 };

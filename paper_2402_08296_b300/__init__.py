@@ -36,8 +36,10 @@ DDG_TIMEOUT = -7
 DDG_PENDING = -8
 DDG_BAD_MESH = -9
 DDG_TOO_LARGE = -10
+DDG_INTERNAL = -11
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA_ERROR", -4: "NOT_CONVERGED",
-                -5: "BREAKDOWN", -8: "PENDING", -9: "BAD_MESH", -10: "TOO_LARGE"}
+                -5: "BREAKDOWN", -6: "BUSY", -7: "TIMEOUT", -8: "PENDING", -9: "BAD_MESH", -10: "TOO_LARGE",
+                -11: "INTERNAL"}
 
 DDG_NONE, DDG_DDM_LU, DDG_DDM_GNN = 0, 1, 2
 DDG_COARSE, DDG_POU_PROLONG, DDG_BF16_WEIGHTS = 1, 2, 4

@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <atomic>
+#include <exception>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -30,6 +33,28 @@ void clear_error();
         int32_t s_ = (call);            \
         if (s_ != DDG_OK) return s_;    \
     } while (0)
+
+// Runs the body of an entry point so that no C++ exception crosses the C ABI: a failed host
+// allocation returns DDG_OOM, any other exception (a thread that cannot be started, say)
+// DDG_INTERNAL, each with its message.
+template <class F>
+int32_t api_guard(F &&body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        set_error("host memory allocation failed");
+        return DDG_OOM;
+    } catch (const std::length_error &e) {
+        set_error(std::string("host allocation too large: ") + e.what());
+        return DDG_OOM;
+    } catch (const std::exception &e) {
+        set_error(std::string("internal error: ") + e.what());
+        return DDG_INTERNAL;
+    } catch (...) {
+        set_error("internal error");
+        return DDG_INTERNAL;
+    }
+}
 
 // every launch site is followed by DDG_LAUNCH_CHECK (or DDG_LAUNCHES(n) for n launches)
 void note_launches(int n);

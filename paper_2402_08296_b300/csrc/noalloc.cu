@@ -82,24 +82,26 @@ using namespace ddg;
 
 extern "C" int32_t ddg_apply_A_dot_noalloc(ddg_problem *p, const double *x_dev, double *y_dev, double *xy_dev,
                                            ddg_stream stream) {
-    clear_error();
-    if (!p || !p->assembled || !x_dev || !y_dev || !xy_dev) {
-        set_error("ddg_apply_A_dot_noalloc: NULL argument or problem not assembled");
-        return DDG_INVALID_ARG;
-    }
-    const int nb = cdiv(p->nf, NOALLOC_T);
-    if (nb > NOALLOC_MAX_BLOCKS) {
-        set_error("ddg_apply_A_dot_noalloc: " + std::to_string(p->nf) + " rows exceed the limit of " +
-                  std::to_string((long long)NOALLOC_MAX_BLOCKS * NOALLOC_T) + " rows");
-        return DDG_TOO_LARGE;
-    }
-    DDG_CU(cudaSetDevice(p->ctx->device));
-    double *partials = nullptr;
-    DDG_TRY(partials_for_device(p->ctx->device, &partials));
-    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
-    k_spmv_dot_noalloc<<<nb, NOALLOC_T, 0, s>>>(p->rowptr, p->col, p->val, x_dev, y_dev, p->nf, partials);
-    DDG_LAUNCH_CHECK();
-    k_dot_final_noalloc<<<1, NOALLOC_T, 0, s>>>(partials, nb, xy_dev);
-    DDG_LAUNCH_CHECK();
-    return DDG_OK;
+    return api_guard([&]() -> int32_t {
+        clear_error();
+        if (!p || !p->assembled || !x_dev || !y_dev || !xy_dev) {
+            set_error("ddg_apply_A_dot_noalloc: NULL argument or problem not assembled");
+            return DDG_INVALID_ARG;
+        }
+        const int nb = cdiv(p->nf, NOALLOC_T);
+        if (nb > NOALLOC_MAX_BLOCKS) {
+            set_error("ddg_apply_A_dot_noalloc: " + std::to_string(p->nf) + " rows exceed the limit of " +
+                      std::to_string((long long)NOALLOC_MAX_BLOCKS * NOALLOC_T) + " rows");
+            return DDG_TOO_LARGE;
+        }
+        DDG_CU(cudaSetDevice(p->ctx->device));
+        double *partials = nullptr;
+        DDG_TRY(partials_for_device(p->ctx->device, &partials));
+        cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
+        k_spmv_dot_noalloc<<<nb, NOALLOC_T, 0, s>>>(p->rowptr, p->col, p->val, x_dev, y_dev, p->nf, partials);
+        DDG_LAUNCH_CHECK();
+        k_dot_final_noalloc<<<1, NOALLOC_T, 0, s>>>(partials, nb, xy_dev);
+        DDG_LAUNCH_CHECK();
+        return DDG_OK;
+    });
 }

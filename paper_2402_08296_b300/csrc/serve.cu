@@ -241,36 +241,77 @@ static int32_t group_step(Server::Group &G, bool *launched) {
     return DDG_OK;
 }
 
-static void loop(Server *S) {
-    cudaSetDevice(S->ctx->device);
-    for (;;) {
-        std::vector<ServeRequest *> admit;
-        std::vector<ServeRequest *> act;
-        {
-            std::unique_lock<std::mutex> lock(S->mu);
-            if (S->stop && S->pending.empty() && S->active.empty()) break;
-            while (!S->pending.empty() && (int)S->active.size() + (int)admit.size() < S->max_active) {
-                ServeRequest *q = S->pending.front();
-                const size_t budget = S->ctx->budget;
-                const bool nothing_running = S->active.empty() && admit.empty();
-                // wait for memory unless nothing runs (then the request proceeds and may fail with DDG_OOM)
-                if (budget && S->reserved + q->est_bytes > budget && !nothing_running) break;
-                S->pending.pop_front();
-                S->reserved += q->est_bytes;
-                q->t_admit = now_ms();
-                admit.push_back(q);
-                S->active.push_back(q);
-            }
-            act = S->active;
+// one pass of the scheduler; false once it has been asked to stop and nothing is left
+static bool loop_once(Server *S) {
+    std::vector<ServeRequest *> admit;
+    std::vector<ServeRequest *> act;
+    {
+        std::unique_lock<std::mutex> lock(S->mu);
+        if (S->stop && S->pending.empty() && S->active.empty()) return false;
+        while (!S->pending.empty() && (int)S->active.size() + (int)admit.size() < S->max_active) {
+            ServeRequest *q = S->pending.front();
+            const size_t budget = S->ctx->budget;
+            const bool nothing_running = S->active.empty() && admit.empty();
+            // wait for memory unless nothing runs (then the request proceeds and may fail with DDG_OOM)
+            if (budget && S->reserved + q->est_bytes > budget && !nothing_running) break;
+            S->pending.pop_front();
+            S->reserved += q->est_bytes;
+            q->t_admit = now_ms();
+            admit.push_back(q);
+            S->active.push_back(q);
         }
-        bool progressed = !admit.empty();
-        for (ServeRequest *q : admit) {
-            int32_t s = start(S, q);
+        act = S->active;
+    }
+    bool progressed = !admit.empty();
+    for (ServeRequest *q : admit) {
+        int32_t s = api_guard([&]() -> int32_t { return start(S, q); });
+        if (s != DDG_OK) finish(S, q, s, last_error_cstr());
+    }
+    for (ServeRequest *q : act) {  // requests on their own (group members are handled below)
+        // (admitted this round: started above, possibly already finished and collected)
+        if (std::find(admit.begin(), admit.end(), q) != admit.end() || !q->run || q->grouped) continue;
+        bool ready = false, done = false;
+        int32_t s = fcg_check(q->run, false, &ready, &done);
+        if (s != DDG_OK) {
+            finish(S, q, s, last_error_cstr());
+            progressed = true;
+            continue;
+        }
+        if (!ready) continue;
+        progressed = true;
+        if (done) {
+            int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
+            q->rep.solve_ms = now_ms() - q->t_admit;  // wall time from admission to the result
+            finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
+        } else {
+            s = fcg_launch_batch(q->run);
             if (s != DDG_OK) finish(S, q, s, last_error_cstr());
         }
-        for (ServeRequest *q : act) {  // requests on their own (group members are handled below)
-            // (admitted this round: started above, possibly already finished and collected)
-            if (std::find(admit.begin(), admit.end(), q) != admit.end() || !q->run || q->grouped) continue;
+    }
+    // fused GNN groups: alternately queue one step of each while fewer than DEPTH are in flight
+    for (bool any = true; any;) {
+        any = false;
+        for (Server::Group &G : S->groups) {
+            if (G.members.empty()) continue;
+            while (G.steps_done < G.steps &&
+                   cudaEventQuery(G.ev_step[G.steps_done % Server::Group::DEPTH]) == cudaSuccess)
+                ++G.steps_done;
+            cudaGetLastError();
+            if (G.steps - G.steps_done >= Server::Group::DEPTH) continue;
+            bool launched = false;
+            int32_t s = api_guard([&]() -> int32_t { return group_step(G, &launched); });
+            if (s != DDG_OK) {  // a launch failed: fail every member
+                std::vector<ServeRequest *> g = G.members;
+                for (ServeRequest *q : g) finish(S, q, s, last_error_cstr());
+                progressed = true;
+                continue;
+            }
+            if (launched) any = progressed = true;
+        }
+    }
+    for (Server::Group &G : S->groups) {
+        for (ServeRequest *q : std::vector<ServeRequest *>(G.members)) {
+            if (!q->marked) continue;
             bool ready = false, done = false;
             int32_t s = fcg_check(q->run, false, &ready, &done);
             if (s != DDG_OK) {
@@ -279,60 +320,32 @@ static void loop(Server *S) {
                 continue;
             }
             if (!ready) continue;
+            q->marked = false;
             progressed = true;
             if (done) {
                 int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
-                q->rep.solve_ms = now_ms() - q->t_admit;  // wall time from admission to the result
+                q->rep.solve_ms = now_ms() - q->t_admit;
                 finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
-            } else {
-                s = fcg_launch_batch(q->run);
-                if (s != DDG_OK) finish(S, q, s, last_error_cstr());
             }
         }
-        // fused GNN groups: alternately queue one step of each while fewer than DEPTH are in flight
-        for (bool any = true; any;) {
-            any = false;
-            for (Server::Group &G : S->groups) {
-                if (G.members.empty()) continue;
-                while (G.steps_done < G.steps &&
-                       cudaEventQuery(G.ev_step[G.steps_done % Server::Group::DEPTH]) == cudaSuccess)
-                    ++G.steps_done;
-                cudaGetLastError();
-                if (G.steps - G.steps_done >= Server::Group::DEPTH) continue;
-                bool launched = false;
-                int32_t s = group_step(G, &launched);
-                if (s != DDG_OK) {  // a launch failed: fail every member
-                    std::vector<ServeRequest *> g = G.members;
-                    for (ServeRequest *q : g) finish(S, q, s, last_error_cstr());
-                    progressed = true;
-                    continue;
-                }
-                if (launched) any = progressed = true;
-            }
-        }
-        for (Server::Group &G : S->groups) {
-            for (ServeRequest *q : std::vector<ServeRequest *>(G.members)) {
-                if (!q->marked) continue;
-                bool ready = false, done = false;
-                int32_t s = fcg_check(q->run, false, &ready, &done);
-                if (s != DDG_OK) {
-                    finish(S, q, s, last_error_cstr());
-                    progressed = true;
-                    continue;
-                }
-                if (!ready) continue;
-                q->marked = false;
-                progressed = true;
-                if (done) {
-                    int32_t fs = fcg_end(q->run, q->x.data(), &q->rep);
-                    q->rep.solve_ms = now_ms() - q->t_admit;
-                    finish(S, q, fs, fs == DDG_OK ? "" : last_error_cstr());
-                }
-            }
-        }
-        if (!progressed) {
-            std::unique_lock<std::mutex> lock(S->mu);
-            S->cv.wait_for(lock, std::chrono::microseconds(S->active.empty() ? 2000 : 30));
+    }
+    if (!progressed) {
+        std::unique_lock<std::mutex> lock(S->mu);
+        S->cv.wait_for(lock, std::chrono::microseconds(S->active.empty() ? 2000 : 30));
+    }
+    return true;
+}
+
+// The scheduler thread.  Calls that allocate host memory for a request are guarded above and
+// fail that request with a status; anything else that throws (host memory exhausted in the
+// scheduler's own bookkeeping) ends only the pass, and the next pass retries.
+static void loop(Server *S) {
+    cudaSetDevice(S->ctx->device);
+    for (;;) {
+        try {
+            if (!loop_once(S)) break;
+        } catch (...) {
+            std::this_thread::sleep_for(std::chrono::milliseconds(1));
         }
     }
 }
@@ -387,110 +400,118 @@ using namespace ddg;
 extern "C" {
 
 int32_t ddg_serve_config(ddg_ctx *c, int32_t max_active, int32_t fuse_gnn, int32_t max_pending) {
-    clear_error();
-    if (!c || max_active < 1 || (fuse_gnn != 0 && fuse_gnn != 1) || max_pending < 1) {
-        set_error("ddg_serve_config: bad arguments");
-        return DDG_INVALID_ARG;
-    }
-    Server *S = server_get(c);
-    std::lock_guard<std::mutex> lock(S->mu);
-    S->max_active = max_active;
-    S->max_pending = max_pending;
-    // the scheduler reads `fuse` when it starts a request: switching only affects later ones
-    S->fuse = fuse_gnn != 0 && S->fuse_ready;
-    return DDG_OK;
+    return api_guard([&]() -> int32_t {
+        clear_error();
+        if (!c || max_active < 1 || (fuse_gnn != 0 && fuse_gnn != 1) || max_pending < 1) {
+            set_error("ddg_serve_config: bad arguments");
+            return DDG_INVALID_ARG;
+        }
+        Server *S = server_get(c);
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->max_active = max_active;
+        S->max_pending = max_pending;
+        // the scheduler reads `fuse` when it starts a request: switching only affects later ones
+        S->fuse = fuse_gnn != 0 && S->fuse_ready;
+        return DDG_OK;
+    });
 }
 
 int32_t ddg_submit(ddg_ctx *c, int32_t n_nodes, const double *xy, int32_t n_tri, const int32_t *tri,
                    const double r[9], const ddg_solve_opts *opts, uint64_t *ticket) {
-    clear_error();
-    if (!c || !xy || !tri || !r || !opts || !ticket || n_nodes < 3 || n_tri < 1) {
-        set_error("ddg_submit: bad arguments");
-        return DDG_INVALID_ARG;
-    }
-    if ((opts->kind == DDG_DDM_GNN && !opts->model) || opts->rtol <= 0.0 || opts->max_iter < 1 ||
-        opts->m_trunc < 1 || opts->overlap < 0) {
-        set_error("ddg_submit: bad solver options");
-        return DDG_INVALID_ARG;
-    }
-    ServeRequest *q = new ServeRequest();
-    q->xy.assign(xy, xy + 2 * (size_t)n_nodes);
-    q->tri.assign(tri, tri + 3 * (size_t)n_tri);
-    std::memcpy(q->r9, r, sizeof(q->r9));
-    q->opts = *opts;
-    q->est_bytes = estimate_bytes(n_nodes, *opts);
-    q->t_submit = now_ms();
-    Server *S = server_get(c);
-    std::lock_guard<std::mutex> lock(S->mu);
-    if ((int)S->pending.size() >= S->max_pending) {
-        delete q;
-        set_error("ddg_submit: the admission queue is full");
-        return DDG_BUSY;
-    }
-    q->ticket = S->next_ticket++;
-    S->live.insert(q->ticket);
-    if (S->t_first_submit < 0.0) S->t_first_submit = q->t_submit;
-    S->pending.push_back(q);
-    *ticket = q->ticket;
-    S->cv.notify_all();
-    return DDG_OK;
+    return api_guard([&]() -> int32_t {
+        clear_error();
+        if (!c || !xy || !tri || !r || !opts || !ticket || n_nodes < 3 || n_tri < 1) {
+            set_error("ddg_submit: bad arguments");
+            return DDG_INVALID_ARG;
+        }
+        if ((opts->kind == DDG_DDM_GNN && !opts->model) || opts->rtol <= 0.0 || opts->max_iter < 1 ||
+            opts->m_trunc < 1 || opts->overlap < 0) {
+            set_error("ddg_submit: bad solver options");
+            return DDG_INVALID_ARG;
+        }
+        ServeRequest *q = new ServeRequest();
+        q->xy.assign(xy, xy + 2 * (size_t)n_nodes);
+        q->tri.assign(tri, tri + 3 * (size_t)n_tri);
+        std::memcpy(q->r9, r, sizeof(q->r9));
+        q->opts = *opts;
+        q->est_bytes = estimate_bytes(n_nodes, *opts);
+        q->t_submit = now_ms();
+        Server *S = server_get(c);
+        std::lock_guard<std::mutex> lock(S->mu);
+        if ((int)S->pending.size() >= S->max_pending) {
+            delete q;
+            set_error("ddg_submit: the admission queue is full");
+            return DDG_BUSY;
+        }
+        q->ticket = S->next_ticket++;
+        S->live.insert(q->ticket);
+        if (S->t_first_submit < 0.0) S->t_first_submit = q->t_submit;
+        S->pending.push_back(q);
+        *ticket = q->ticket;
+        S->cv.notify_all();
+        return DDG_OK;
+    });
 }
 
 int32_t ddg_poll(ddg_ctx *c, uint64_t ticket, ddg_solve_report *report, double *x_host) {
-    clear_error();
-    if (!c) {
-        set_error("ddg_poll: NULL context");
-        return DDG_INVALID_ARG;
-    }
-    Server *S = server_get(c);
-    ServeRequest *q = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(S->mu);
-        auto it = S->finished.find(ticket);
-        if (it == S->finished.end()) {
-            if (!S->live.count(ticket)) {
-                set_error("ddg_poll: unknown or already collected ticket");
-                return DDG_INVALID_ARG;
-            }
-            return DDG_PENDING;
+    return api_guard([&]() -> int32_t {
+        clear_error();
+        if (!c) {
+            set_error("ddg_poll: NULL context");
+            return DDG_INVALID_ARG;
         }
-        q = it->second;
-        S->finished.erase(it);
-        S->live.erase(ticket);
-    }
-    if (report) *report = q->rep;
-    if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), sizeof(double) * q->x.size());
-    int32_t st = q->status;
-    if (!q->err.empty()) set_error(q->err);
-    delete q;
-    return st;
+        Server *S = server_get(c);
+        ServeRequest *q = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            auto it = S->finished.find(ticket);
+            if (it == S->finished.end()) {
+                if (!S->live.count(ticket)) {
+                    set_error("ddg_poll: unknown or already collected ticket");
+                    return DDG_INVALID_ARG;
+                }
+                return DDG_PENDING;
+            }
+            q = it->second;
+            S->finished.erase(it);
+            S->live.erase(ticket);
+        }
+        if (report) *report = q->rep;
+        if (x_host && !q->x.empty()) std::memcpy(x_host, q->x.data(), sizeof(double) * q->x.size());
+        int32_t st = q->status;
+        if (!q->err.empty()) set_error(q->err);
+        delete q;
+        return st;
+    });
 }
 
 int32_t ddg_serve_stats(ddg_ctx *c, ddg_serve_summary *out) {
-    clear_error();
-    if (!c || !out) {
-        set_error("ddg_serve_stats: bad arguments");
-        return DDG_INVALID_ARG;
-    }
-    Server *S = server_get(c);
-    std::lock_guard<std::mutex> lock(S->mu);
-    std::memset(out, 0, sizeof(*out));
-    out->completed = S->completed;
-    out->failed = S->failed;
-    out->pending = S->pending.size();
-    out->active = S->active.size();
-    out->reserved_bytes = S->reserved;
-    out->device_bytes = c->in_use;
-    if (!S->latencies.empty()) {
-        std::vector<double> l = S->latencies;
-        std::sort(l.begin(), l.end());
-        auto pct = [&](double f) { return l[std::min(l.size() - 1, (size_t)(f * (l.size() - 1) + 0.5))]; };
-        out->p50_ms = pct(0.50);
-        out->p99_ms = pct(0.99);
-        double span = S->t_last_done - S->t_first_submit;
-        out->solves_per_s = span > 0.0 ? S->completed / (span / 1e3) : 0.0;
-    }
-    return DDG_OK;
+    return api_guard([&]() -> int32_t {
+        clear_error();
+        if (!c || !out) {
+            set_error("ddg_serve_stats: bad arguments");
+            return DDG_INVALID_ARG;
+        }
+        Server *S = server_get(c);
+        std::lock_guard<std::mutex> lock(S->mu);
+        std::memset(out, 0, sizeof(*out));
+        out->completed = S->completed;
+        out->failed = S->failed;
+        out->pending = S->pending.size();
+        out->active = S->active.size();
+        out->reserved_bytes = S->reserved;
+        out->device_bytes = c->in_use;
+        if (!S->latencies.empty()) {
+            std::vector<double> l = S->latencies;
+            std::sort(l.begin(), l.end());
+            auto pct = [&](double f) { return l[std::min(l.size() - 1, (size_t)(f * (l.size() - 1) + 0.5))]; };
+            out->p50_ms = pct(0.50);
+            out->p99_ms = pct(0.99);
+            double span = S->t_last_done - S->t_first_submit;
+            out->solves_per_s = span > 0.0 ? S->completed / (span / 1e3) : 0.0;
+        }
+        return DDG_OK;
+    });
 }
 
 }  // extern "C"
