@@ -52,7 +52,10 @@ __device__ __forceinline__ void block_parts(const double (&v)[NV], int nv, doubl
 #pragma unroll
         for (int k = 1; k < KT / 32; ++k) t += sh[j * KT + 32 * k + lane];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) out[j * stride] = t;
+        if (lane == 0) {
+            out[j * stride] = t;
+            __threadfence();  // each writer orders its partial before the block's ticket (last_block)
+        }
     }
 }
 
