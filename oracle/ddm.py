@@ -94,10 +94,13 @@ class DDMGNN:
 
 
 def pcg(A, b: np.ndarray, M, tol: float, max_iter: int):
-    """Algorithm 1 with u_0 = 0; returns (u, iterations, history of |r|/|b|)."""
+    """Algorithm 1 with u_0 = 0; returns (u, iterations, history of |r|/|b|).
+    b = 0 returns u = 0 after zero iterations (reading C-20: |r|/|b| is undefined there)."""
     u = np.zeros_like(b)
     r = b.copy()
     bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return u, 0, []
     z = M(r)
     p = z.copy()
     rho = r @ z
@@ -119,10 +122,13 @@ def pcg(A, b: np.ndarray, M, tol: float, max_iter: int):
 
 
 def fcg(A, b: np.ndarray, M, tol: float, max_iter: int, m: int):
-    """Flexible CG with truncation m and u_0 = 0; returns (u, iterations, history of |r|/|b|)."""
+    """Flexible CG with truncation m and u_0 = 0; returns (u, iterations, history of |r|/|b|).
+    b = 0 returns u = 0 after zero iterations (reading C-20)."""
     u = np.zeros_like(b)
     r = b.copy()
     bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return u, 0, []
     P, Q, PQ = [], [], []
     hist = []
     for it in range(1, max_iter + 1):

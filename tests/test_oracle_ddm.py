@@ -67,6 +67,16 @@ def test_fcg_with_fixed_spd_preconditioner_matches_pcg(small):
         assert np.allclose(hp[:k - 1], hf[:k - 1], rtol=1e-4)
 
 
+def test_zero_right_hand_side_has_the_zero_solution(small):
+    """A is SPD, so A u = 0 only for u = 0; both drivers return it without iterating (reading C-20)."""
+    P = small
+    D = pt.decompose(P, 4, 1)
+    asm = ddm.TwoLevelASM(P, D)
+    z = np.zeros(P.n_free)
+    for u, it, h in (ddm.pcg(P.A, z, asm.apply_lu, 1e-6, 50), ddm.fcg(P.A, z, asm.apply_lu, 1e-6, 50, 10)):
+        assert it == 0 and h == [] and not np.any(u)
+
+
 def test_unpreconditioned_cg_finite_termination():
     m = synth.square_mesh(5, seed=0)
     P = fem.assemble(m.xy, m.tri, coeffs=synth.poly_coeffs(0))
