@@ -150,12 +150,50 @@ def _host(a, dtype):
     return arr, arr.ctypes.data_as(_p)
 
 
-def _dev(x):
+def _host_n(a, dtype, n: int, what: str):
+    """_host with a length check: the library reads or writes exactly n values there."""
+    arr, ptr = _host(a, dtype)
+    if arr.size != n:
+        raise ValueError(f"{what}: {arr.size} values, expected {n}")
+    return arr, ptr
+
+
+def _rows(a, dtype, width: int, what: str):
+    """_host for an (n, width) array; returns (array, address, n)."""
+    arr, ptr = _host(a, dtype)
+    if arr.ndim != 2 or arr.shape[1] != width:
+        raise ValueError(f"{what}: shape {arr.shape}, expected (n, {width})")
+    return arr, ptr, arr.shape[0]
+
+
+def _dev(x, n: int | None = None, what: str = "device array"):
+    """Address of a device array: a contiguous CUDA torch tensor of float64 with at least n
+    elements, or a raw device address (an int), which the caller vouches for."""
     if x is None:
         return None
     if isinstance(x, int):
         return _p(x)
+    if not (hasattr(x, "data_ptr") and hasattr(x, "is_cuda") and hasattr(x, "dtype")):
+        raise TypeError(f"{what}: expected a CUDA torch tensor or a device address, got {type(x).__name__}")
+    import torch
+    if x.dtype != torch.float64:
+        raise TypeError(f"{what}: dtype {x.dtype}, expected torch.float64")
+    if not x.is_cuda:
+        raise ValueError(f"{what}: not on a CUDA device")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: not contiguous")
+    if n is not None and x.numel() < n:
+        raise ValueError(f"{what}: {x.numel()} elements, expected at least {n}")
     return _p(x.data_ptr())
+
+
+def _devs(p, **arrays):
+    """Checks the device arrays' types first (no library call), then their sizes against the
+    problem: each keyword maps a name to (tensor, key of ddg_problem_info or a number)."""
+    for name, (t, _) in arrays.items():
+        _dev(t, None, name)
+    info = ddg_problem_info(p)
+    return [_dev(t, info[k] if isinstance(k, str) else k, name) for name, (t, k) in arrays.items()]
 
 
 CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
@@ -212,14 +250,13 @@ def ddg_launch_count() -> int:
 
 
 def ddg_mesh_upload(ctx, xy, tri, dirichlet=None):
-    xy_a, xy_p = _host(xy, np.float64)
-    tri_a, tri_p = _host(tri, np.int32)
+    xy_a, xy_p, n = _rows(xy, np.float64, 2, "xy")
+    tri_a, tri_p, t = _rows(tri, np.int32, 3, "tri")
     d_p = None
     if dirichlet is not None:
-        d_a, d_p = _host(dirichlet, np.uint8)
+        d_a, d_p = _host_n(dirichlet, np.uint8, n, "dirichlet")
     h = _p()
-    _check(lib.ddg_mesh_upload(ctx, xy_a.shape[0], xy_p, tri_a.shape[0], tri_p, d_p, ctypes.byref(h)),
-           "ddg_mesh_upload")
+    _check(lib.ddg_mesh_upload(ctx, n, xy_p, t, tri_p, d_p, ctypes.byref(h)), "ddg_mesh_upload")
     return h
 
 
@@ -228,14 +265,14 @@ def ddg_problem_destroy(p) -> None:
 
 
 def ddg_assemble_poly(p, r) -> None:
-    r_a, r_p = _host(r, np.float64)
-    assert r_a.shape == (9,)
+    r_a, r_p = _host_n(r, np.float64, 9, "r")
     _check(lib.ddg_assemble_poly(p, r_p), "ddg_assemble_poly")
 
 
 def ddg_assemble_nodal(p, f, g) -> None:
-    f_a, f_p = _host(f, np.float64)
-    g_a, g_p = _host(g, np.float64)
+    n = ddg_problem_info(p)["n_nodes"]
+    f_a, f_p = _host_n(f, np.float64, n, "f")
+    g_a, g_p = _host_n(g, np.float64, n, "g")
     _check(lib.ddg_assemble_nodal(p, f_p, g_p), "ddg_assemble_nodal")
 
 
@@ -263,7 +300,7 @@ def ddg_matrix_download(p):
 def ddg_partition(p, K: int, overlap_layers: int, part=None) -> None:
     pp = None
     if part is not None:
-        part_a, pp = _host(part, np.int32)
+        part_a, pp = _host_n(part, np.int32, ddg_problem_info(p)["n_free"], "part")
     _check(lib.ddg_partition(p, K, overlap_layers, pp), "ddg_partition")
 
 
@@ -304,8 +341,7 @@ def ddg_model_create(ctx, kbar: int, d: int, alpha: float, w=None, seed: int = 0
     n_w = kbar * (11 * d * d + 15 * d + 1)
     wp = None
     if w is not None:
-        w_a, wp = _host(w, np.float32)
-        assert w_a.size == n_w
+        w_a, wp = _host_n(w, np.float32, n_w, "w")
     h = _p()
     _check(lib.ddg_model_create(ctx, kbar, d, alpha, wp, n_w, seed, ctypes.byref(h)), "ddg_model_create")
     return h
@@ -331,22 +367,24 @@ def ddg_setup_precond(p, kind: int, model=None, flags: int = DDG_COARSE) -> None
 
 
 def ddg_precondition(p, r_dev, z_dev, stream=None) -> None:
-    _check(lib.ddg_precondition(p, _dev(r_dev), _dev(z_dev), _stream(stream, r_dev, z_dev)), "ddg_precondition")
+    r_p, z_p = _devs(p, r_dev=(r_dev, "n_free"), z_dev=(z_dev, "n_free"))
+    _check(lib.ddg_precondition(p, r_p, z_p, _stream(stream, r_dev, z_dev)), "ddg_precondition")
 
 
 def ddg_local_corrections(p, r_dev, corr_dev, s_dev, stream=None) -> None:
-    _check(lib.ddg_local_corrections(p, _dev(r_dev), _dev(corr_dev), _dev(s_dev), _stream(stream, r_dev)),
-           "ddg_local_corrections")
+    r_p, c_p, s_p = _devs(p, r_dev=(r_dev, "n_free"), corr_dev=(corr_dev, "sum_k"), s_dev=(s_dev, "K"))
+    _check(lib.ddg_local_corrections(p, r_p, c_p, s_p, _stream(stream, r_dev)), "ddg_local_corrections")
 
 
 def ddg_apply_A(p, x_dev, y_dev, stream=None) -> None:
-    _check(lib.ddg_apply_A(p, _dev(x_dev), _dev(y_dev), _stream(stream, x_dev, y_dev)), "ddg_apply_A")
+    x_p, y_p = _devs(p, x_dev=(x_dev, "n_free"), y_dev=(y_dev, "n_free"))
+    _check(lib.ddg_apply_A(p, x_p, y_p, _stream(stream, x_dev, y_dev)), "ddg_apply_A")
 
 
 def ddg_apply_A_dot_noalloc(p, x_dev, y_dev, xy_dev, stream=None) -> None:
     """y = A x and x . y into the one-element device tensor xy_dev, with no device allocation."""
-    _check(lib.ddg_apply_A_dot_noalloc(p, _dev(x_dev), _dev(y_dev), _dev(xy_dev), _stream(stream, x_dev, y_dev)),
-           "ddg_apply_A_dot_noalloc")
+    x_p, y_p, xy_p = _devs(p, x_dev=(x_dev, "n_free"), y_dev=(y_dev, "n_free"), xy_dev=(xy_dev, 1))
+    _check(lib.ddg_apply_A_dot_noalloc(p, x_p, y_p, xy_p, _stream(stream, x_dev, y_dev)), "ddg_apply_A_dot_noalloc")
 
 
 def ddg_train_local_model(p, m, steps: int, batch: int = 32, lr: float = 1e-2, clip: float = 1e-2,
@@ -361,9 +399,10 @@ def ddg_train_local_model(p, m, steps: int, batch: int = 32, lr: float = 1e-2, c
 def ddg_train_loss_grad(p, m, r_dev, graphs, n_w: int):
     """(loss, flat gradient) of the training loss for the given local graphs with residual r_dev."""
     g_a, g_p = _host(graphs, np.int32)
+    (r_p,) = _devs(p, r_dev=(r_dev, "n_free"))
     loss = _f64()
     grad = np.zeros(n_w, np.float32)
-    _check(lib.ddg_train_loss_grad(p, m, _dev(r_dev), g_p, g_a.size, ctypes.byref(loss), grad.ctypes.data_as(_p)),
+    _check(lib.ddg_train_loss_grad(p, m, r_p, g_p, g_a.size, ctypes.byref(loss), grad.ctypes.data_as(_p)),
            "ddg_train_loss_grad")
     return float(loss.value), grad
 
@@ -373,7 +412,7 @@ def ddg_fcg_solve(p, rtol: float, max_iter: int, m_trunc: int, x0=None, want_x: 
     info = ddg_problem_info(p)
     x0p = None
     if x0 is not None:
-        x0_a, x0p = _host(x0, np.float64)
+        x0_a, x0p = _host_n(x0, np.float64, info["n_free"], "x0")
     x = np.zeros(info["n_nodes"], np.float64) if want_x else None
     rep = ddg_solve_report()
     st = lib.ddg_fcg_solve(p, x0p, rtol, max_iter, m_trunc, x.ctypes.data_as(_p) if want_x else None,
@@ -393,26 +432,41 @@ def ddg_fcg_history(p) -> np.ndarray:
     return out
 
 
+_TICKET_NODES = {}  # (context address, ticket) -> nodes of the submitted mesh, until collected
+
+
+def _addr(handle) -> int:
+    return int(handle.value or 0) if hasattr(handle, "value") else int(handle or 0)
+
+
 def ddg_submit(ctx, xy, tri, r, kind: int, model=None, flags: int = DDG_COARSE, K: int = 0, overlap: int = 2,
                rtol: float = 1e-6, max_iter: int = 2000, m_trunc: int = 10) -> int:
     """Queue a solve; returns its ticket."""
-    xy_a, xy_p = _host(xy, np.float64)
-    tri_a, tri_p = _host(tri, np.int32)
-    r_a, r_p = _host(r, np.float64)
+    xy_a, xy_p, n = _rows(xy, np.float64, 2, "xy")
+    tri_a, tri_p, nt = _rows(tri, np.int32, 3, "tri")
+    r_a, r_p = _host_n(r, np.float64, 9, "r")
     o = ddg_solve_opts(kind, flags, model, K, overlap, rtol, max_iter, m_trunc)
     t = _u64()
-    _check(lib.ddg_submit(ctx, xy_a.shape[0], xy_p, tri_a.shape[0], tri_p, r_p, ctypes.byref(o), ctypes.byref(t)),
-           "ddg_submit")
+    _check(lib.ddg_submit(ctx, n, xy_p, nt, tri_p, r_p, ctypes.byref(o), ctypes.byref(t)), "ddg_submit")
+    _TICKET_NODES[(_addr(ctx), int(t.value))] = n
     return int(t.value)
 
 
 def ddg_poll(ctx, ticket: int, n_nodes: int | None = None):
-    """(status, report dict, x or None); status DDG_PENDING while the request runs."""
+    """(status, report dict, x or None); status DDG_PENDING while the request runs.
+
+    With n_nodes given, x receives the solution; the buffer is sized from the mesh that
+    ddg_submit sent, and a different n_nodes is refused (the library writes that many values)."""
+    key = (_addr(ctx), int(ticket))
+    known = _TICKET_NODES.get(key)
+    if n_nodes and known is not None and n_nodes != known:
+        raise ValueError(f"ddg_poll: n_nodes {n_nodes}, but ticket {ticket} was submitted with {known} nodes")
     rep = ddg_solve_report()
-    x = np.zeros(n_nodes, np.float64) if n_nodes else None
+    x = np.zeros(known if known is not None else n_nodes, np.float64) if n_nodes else None
     st = lib.ddg_poll(ctx, ticket, ctypes.byref(rep), x.ctypes.data_as(_p) if x is not None else None)
     if st == DDG_PENDING:
         return st, None, None
+    _TICKET_NODES.pop(key, None)
     if st == DDG_INVALID_ARG:
         raise DdgError(st, "ddg_poll")
     return st, rep.as_dict(), x
