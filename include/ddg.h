@@ -274,8 +274,8 @@ int32_t ddg_fcg_solve(ddg_problem *p, const double *x0, double rtol, int32_t max
 
 /* The residual history of the problem's last ddg_fcg_solve: rel_host[i] =
  * |r_(i+1)| / |b| (the recursive residual after iteration i + 1), for the
- * first min(n, *count) iterations; *count = iterations recorded.  Host buffer,
- * caller-owned.  Errors: DDG_INVALID_ARG. */
+ * first min(n, *count) iterations; *count = iterations recorded (the first
+ * 1,048,576 at most).  Host buffer, caller-owned.  Errors: DDG_INVALID_ARG. */
 int32_t ddg_fcg_history(ddg_problem *p, double *rel_host, int32_t n, int32_t *count);
 
 /* ---- serving (continuous batching of independent solves) ------------- */

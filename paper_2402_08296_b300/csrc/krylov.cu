@@ -28,6 +28,7 @@ constexpr int RB = 1184;           // grid of the norm kernels; bound on the red
 constexpr int PUG = 592;           // grid of the direction update (4 CTAs of 256 per SM)
 constexpr int MAXM = 16;           // largest truncation
 constexpr int POLL = 4;            // iterations between stop-flag polls
+constexpr int HIST_MAX = 1 << 20;  // iterations a solve's residual history keeps at most
 constexpr int OFF_MD = 0;          // partial-sum regions of kpart: multidot, then SpMV dots, then |r|^2
 
 // scalar slots (kscal) and flags (kflag)
@@ -571,12 +572,15 @@ struct FcgRun {
             DDG_TRY(dalloc(c, p->a_kry, &p->kflag, F_COUNT));
             p->kr_m = m;
         }
-        if (p->khist_cap < max_iter) {  // residual history of the solve (kept for ddg_fcg_history)
+        // residual history of the solve (kept for ddg_fcg_history): the first HIST_MAX iterations
+        // at most, so that a large max_iter does not reserve device memory it will not use
+        const int hist_need = std::min(max_iter, HIST_MAX);
+        if (p->khist_cap < hist_need) {
             dfree_all(c, p->a_hist);
             p->khist = nullptr;
             p->khist_cap = 0;
-            DDG_TRY(dalloc(c, p->a_hist, &p->khist, (size_t)max_iter));
-            p->khist_cap = max_iter;
+            DDG_TRY(dalloc(c, p->a_hist, &p->khist, (size_t)hist_need));
+            p->khist_cap = hist_need;
         }
         p->khist_n = 0;
         x = p->kx; r = p->kr; z = p->kz; P = p->kP; Q = p->kQ; scal = p->kscal; part = p->kpart;
