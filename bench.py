@@ -551,7 +551,7 @@ def oracle_sample(a, budget_s: float):
         hbar = pt.mean_edge_length(P.xy, P.tri)
         t_setup = time.perf_counter() - t0
         r = P.b
-        done, t_dss = 0, 0.0
+        done, t_dss, t_serial = 0, 0.0, 0.0
         # at least one round of subdomains, even when assembly and decomposition of a large mesh
         # alone use up the budget
         while done < len(Dd.sets) and (done == 0 or t_setup + t_dss < budget_s):
@@ -563,32 +563,47 @@ def oracle_sample(a, budget_s: float):
                 s = np.linalg.norm(r[S])
                 jobs.append((g.xy, g.n_int, g.src, g.dst, r[S] / s, W, hbar))
             t1 = time.perf_counter()
-            pool.map(_oracle_dss, jobs, chunksize=1)
+            t_serial += sum(pool.map(_oracle_dss, jobs, chunksize=1))   # each worker's own, single-threaded time
             t_dss += time.perf_counter() - t1
             done += len(jobs)
     finally:
         pool.terminate()
         pool.join()
     per_apply = t_dss / done * w.K
-    return {"t_setup_s": t_setup, "per_precond_s": per_apply, "subdomains_sampled": done, "K": w.K,
-            "cores": cores}
+    return {"t_setup_s": t_setup, "per_precond_s": per_apply, "per_precond_1thread_s": t_serial / done * w.K,
+            "subdomains_sampled": done, "K": w.K, "cores": cores, "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
 
 
 def run_reference(a, rank):
     if rank != 0:
         return None
-    times = []
+    times, times_1t = [], []
     samp = None
     for _ in range(a.warmup + a.steps):
         samp = oracle_sample(a, a.cpu_seconds / max(1, a.warmup + a.steps))
         times.append(samp["t_setup_s"] + a.ref_iterations * samp["per_precond_s"])
+        times_1t.append(samp["t_setup_s"] + a.ref_iterations * samp["per_precond_1thread_s"])
     t = np.array(times[a.warmup:])
     v = 1.0 / float(t.mean())
+    v_1t = 1.0 / float(np.mean(times_1t[a.warmup:]))
     return {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": float(t.mean() * 1e3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": a.workload, "kbar": KBAR, "d": D, "tol": a.tol},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": samp["cores"], "kind": "oracle",
+                             "value_1thread": v_1t, "cpu_model": samp["cpu_model"], "nproc": os.cpu_count(),
                              "sample": f"assembly + decomposition + FP64 DSS on {samp['subdomains_sampled']} of "
                                        f"{samp['K']} subdomains ({samp['cores']} single-threaded worker "
                                        f"processes), scaled to {a.ref_iterations} preconditioner applications"},
@@ -623,7 +638,9 @@ def main():
         its = int(np.median(out["gnn"]["iterations"]))
         s = oracle_sample(a, a.cpu_seconds)
         t = s["t_setup_s"] + its * s["per_precond_s"]
+        t_1t = s["t_setup_s"] + its * s["per_precond_1thread_s"]
         out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": s["cores"], "kind": "oracle",
+                               "value_1thread": 1.0 / t_1t, "cpu_model": s["cpu_model"], "nproc": os.cpu_count(),
                                "sample": f"assembly + decomposition + FP64 DSS on {s['subdomains_sampled']} of "
                                          f"{s['K']} subdomains ({s['cores']} single-threaded worker processes), "
                                          f"scaled to {its} preconditioner applications (the GPU's iteration count)"}

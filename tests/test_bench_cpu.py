@@ -21,6 +21,7 @@ def test_reference_arm_prints_one_json_line():
     assert rec["config"]["workload"] == "square2k"
     cb = rec["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == rec["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert 0 < cb["value_1thread"] <= cb["value"] * 1.5 and cb["cpu_model"] and cb["nproc"] >= 1
     assert rec["e2e"] == {"value": rec["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
 
@@ -30,4 +31,4 @@ def test_oracle_sample_takes_a_round_of_subdomains_even_without_budget():
     import bench
     s = bench.oracle_sample(types.SimpleNamespace(workload="square2k", seed=0), 0.0)
     assert 1 <= s["subdomains_sampled"] <= s["K"]
-    assert s["per_precond_s"] > 0 and s["t_setup_s"] > 0
+    assert s["per_precond_s"] > 0 and s["t_setup_s"] > 0 and s["per_precond_1thread_s"] > 0
