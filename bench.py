@@ -59,6 +59,8 @@ def args_parse():
     ap.add_argument("--m", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="also measure the FP32/FP64 FMA rates with the library's probe (roofline context)")
     ap.add_argument("--ref-iterations", type=int, default=70,
                     help="reference arm: preconditioner applications a solve is scaled to (the DDM-GNN "
                          "iteration count of star100k with the committed weights)")
@@ -634,6 +636,9 @@ def main():
     out = run_ours(a, rank, world, local_rank)
     if out is None:
         return
+    if a.probe_peaks:
+        import paper_2402_08296_b300 as ddg
+        out["roofline"]["fma_probe"] = ddg.ddg_probe_fma_peaks(local_rank)
     if world == 1 and not a.no_cpu_baseline:
         its = int(np.median(out["gnn"]["iterations"]))
         s = oracle_sample(a, a.cpu_seconds)

@@ -123,6 +123,7 @@ _SIGS = {
     "ddg_serve_stats": [_p, ctypes.POINTER(ddg_serve_summary)],
     "ddg_fcg_solve": [_p, _p, _f64, _i32, _i32, _p, ctypes.POINTER(ddg_solve_report)],
     "ddg_fcg_history": [_p, _p, _i32, ctypes.POINTER(_i32)],
+    "ddg_probe_fma_peaks": [_i32, ctypes.POINTER(_f64), ctypes.POINTER(_f64)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -430,6 +431,13 @@ def ddg_fcg_history(p) -> np.ndarray:
     if cnt.value:
         _check(lib.ddg_fcg_history(p, out.ctypes.data_as(_p), cnt.value, ctypes.byref(cnt)), "ddg_fcg_history")
     return out
+
+
+def ddg_probe_fma_peaks(device: int = 0) -> dict:
+    """FP32 and FP64 FMA rates (TFLOP/s) this GPU reaches (include/ddg_probe.h)."""
+    f32, f64 = _f64(), _f64()
+    _check(lib.ddg_probe_fma_peaks(device, ctypes.byref(f32), ctypes.byref(f64)), "ddg_probe_fma_peaks")
+    return {"fp32_tflops": float(f32.value), "fp64_tflops": float(f64.value)}
 
 
 _TICKET_NODES = {}  # (context address, ticket) -> nodes of the submitted mesh, until collected

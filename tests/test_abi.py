@@ -7,8 +7,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    with open(os.path.join(ROOT, "include", "ddg.h")) as fh:
-        text = fh.read()
+    text = ""
+    inc = os.path.join(ROOT, "include")
+    for name in sorted(os.listdir(inc)):
+        if name.endswith(".h"):
+            with open(os.path.join(inc, name)) as fh:
+                text += fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(ddg_[a-z0-9_]+)\s*\(", text)))
 
@@ -70,6 +74,7 @@ def test_null_handles_are_refused_with_a_status():
         "ddg_serve_stats": (nul, nul),
         "ddg_fcg_solve": (nul, nul, 1e-6, 10, 10, nul, nul),
         "ddg_fcg_history": (nul, nul, 0, nul),
+        "ddg_probe_fma_peaks": (0, nul, nul),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == ddg.DDG_INVALID_ARG, name
