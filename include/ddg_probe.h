@@ -3,7 +3,7 @@
  *
  * Measures the FP32 and FP64 fused multiply-add rates the GPU reaches, the
  * ALU peaks against which the GNN kernel (FP32, Section III-B, Eqs. 18-22)
- * and the Krylov kernels (FP64, Algorithm 1) are judged.  No passage of the
+ * and the Krylov kernels (FP64, Algorithm 1) are measured.  No passage of the
  * paper corresponds to this call; it exists for measurement.
  */
 #ifndef DDG_PROBE_H

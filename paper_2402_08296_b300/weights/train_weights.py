@@ -6,13 +6,13 @@ two overlap layers; ``ddg_train_local_model`` harvests the residuals of
 DDM-LU preconditioned CG on the domain and trains the model on the resulting
 local problems (Adam, lr 1e-2, gradient-norm clip 1e-2, plateau decay).  The
 Adam state lives in the model, so the meshes form one optimisation; the
-learning rate drops x0.1 when the mean loss of a round over all meshes stops
+learning rate drops x0.1 when the mean loss of a pass over all meshes stops
 improving.
 
 Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15 [--kbar 30]
     [--init weights.npy --lr 1e-3]
 Writes dss_k{kbar}_d10.npy (flat float32 weights, layout of include/ddg.h): of the weights after
-every round, those with which DDM-GNN FCG needs the fewest iterations on a held-out domain.
+every pass, those with which DDM-GNN FCG needs the fewest iterations on a held-out domain.
 """
 from __future__ import annotations
 
@@ -37,14 +37,14 @@ def main():
     ap.add_argument("--minutes", type=float, default=15.0)
     ap.add_argument("--meshes", type=int, default=8)
     ap.add_argument("--nodes", type=int, default=30000)
-    ap.add_argument("--steps", type=int, default=200, help="optimiser steps per mesh and round")
+    ap.add_argument("--steps", type=int, default=200, help="optimiser steps per mesh and pass")
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--harvest", type=int, default=60)
     ap.add_argument("--kbar", type=int, default=30, help="message-passing blocks (Section III-B)")
     ap.add_argument("--init", default=None, help="start from these flat weights instead of Xavier")
     ap.add_argument("--lr", type=float, default=1e-2, help="initial learning rate")
     ap.add_argument("--val-nodes", type=int, default=50000,
-                    help="held-out star domain on which every round's weights are judged by FCG iterations")
+                    help="held-out star domain on which the weights of every training pass are scored by FCG iterations")
     ap.add_argument("--out", default=None)
     ap.add_argument("--log", default=None)
     a = ap.parse_args()
@@ -87,7 +87,7 @@ def main():
             rep = ddg.ddg_train_local_model(p, model, steps=a.steps, batch=a.batch, lr=lr, clip=1e-2,
                                             harvest_iters=a.harvest, seed=1000 * rnd + i)
             losses.append(rep["loss_last"])
-            print(f"round {rnd} mesh {i} samples {rep['samples']} loss {rep['loss_first']:.3e} -> "
+            print(f"pass {rnd} mesh {i} samples {rep['samples']} loss {rep['loss_first']:.3e} -> "
                   f"{rep['loss_last']:.3e} lr {lr:.1e} {rep['ms'] / 1e3:.1f}s t {time.time() - t0:.0f}s",
                   file=log, flush=True)
             if time.time() - t0 > 60.0 * a.minutes:
@@ -95,7 +95,7 @@ def main():
         its = val_iterations()
         if its < best_it:
             best_it, best_w = its, ddg.ddg_model_get_weights(model, n_w)
-        print(f"round {rnd} held-out FCG iterations {its} (best {best_it})", file=log, flush=True)
+        print(f"pass {rnd} held-out FCG iterations {its} (best {best_it})", file=log, flush=True)
         mean = float(np.mean(losses))
         if mean < 0.99 * best:
             best, stale = mean, 0
@@ -105,7 +105,7 @@ def main():
                 lr, stale = lr * 0.1, 0
         rnd += 1
     np.save(a.out, best_w)
-    print(f"saved {a.out} after {rnd} rounds (held-out FCG iterations {best_it})", file=log, flush=True)
+    print(f"saved {a.out} after {rnd} passes (held-out FCG iterations {best_it})", file=log, flush=True)
     for p in problems + [val]:
         ddg.ddg_problem_destroy(p)
     ddg.ddg_model_destroy(model)
