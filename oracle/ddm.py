@@ -157,3 +157,20 @@ def fcg(A, b: np.ndarray, M, tol: float, max_iter: int, m: int):
 
 def true_relative_residual(A, b, u) -> float:
     return float(np.linalg.norm(b - A @ u) / np.linalg.norm(b))
+
+
+def condition_estimate(A, solve=None, iters: int = 8) -> float:
+    """Estimate of the 2-norm condition number of the SPD matrix A, for the solution check of
+    reading C-19 (|x - x*| / |x*| <= kappa |b - A x| / |b|): the Gershgorin bound on the
+    largest eigenvalue (max absolute row sum, never below it) over the smallest eigenvalue,
+    taken as the Rayleigh quotient of `iters` steps of inverse iteration from the constant
+    vector.  `solve(v)` returns A^-1 v (default: scipy's sparse LU, for small A)."""
+    lam_max = float(abs(A).sum(axis=1).max())
+    if solve is None:
+        solve = spla.splu(A.tocsc()).solve
+    v = np.ones(A.shape[0])
+    for _ in range(iters):
+        v = solve(v)
+        v /= np.linalg.norm(v)
+    lam_min = float(v @ (A @ v))
+    return lam_max / lam_min

@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import ddm, dss, fem, partition as pt
-from helpers import gpu_setup, oracle_setup, rel
+from helpers import assert_close, gpu_setup, oracle_setup, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,7 @@ def _check_against_oracle(P, Dd, W, alpha, r, corr, s):
             continue
         g = pt.local_graph(P, S, adj)
         ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, KBAR, D, alpha, hbar)
-        assert rel(got, ref) < 1e-4, (i, rel(got, ref))
+        assert_close(got, ref, 1e-4, i)
 
 
 @pytest.mark.parametrize("schedule,chunk_t", SCHEDULES)

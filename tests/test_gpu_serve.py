@@ -1,11 +1,17 @@
 """Serving: requests that arrive while others run are admitted and overlap on the GPU,
-and every result equals the stand-alone solve of the same problem (bitwise)."""
+every result equals the stand-alone solve of the same problem (bitwise), and the oracle
+confirms every served solution (true relative residual of Algorithm 1's stopping test)."""
+import os
 import time
 
 import numpy as np
 import pytest
 
 import synth
+from oracle import ddm, fem, partition as pt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +40,8 @@ def test_results_alone_equal_results_in_the_mix(mode, monkeypatch):
     monkeypatch.setenv("DDG_GNN_SCHEDULE", "3")
     monkeypatch.setenv("DDG_GNN_CHUNK_T", "128")
     ctx = ddg.ddg_create(0)
-    W = synth.dss_weights(30, 10, 21, bias_scale=0.05)
+    # the trained weights, so that the DDM-GNN requests converge and the oracle can judge them
+    W = np.load(WEIGHTS).astype(np.float32)
     m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, W)
     try:
         reqs = []
@@ -58,11 +65,23 @@ def test_results_alone_equal_results_in_the_mix(mode, monkeypatch):
         tickets = [ddg.ddg_submit(ctx, mesh.xy, mesh.tri, r, kind, m if kind == ddg.DDG_DDM_GNN else None,
                                   max_iter=600) for mesh, r, kind in reqs]
         res = _wait(ddg, ctx, tickets, [mesh.n for mesh, _, _ in reqs])
-        for t, (rep_a, x_a) in zip(tickets, alone):
+        for t, (rep_a, x_a), (mesh, r, kind) in zip(tickets, alone, reqs):
             st, rep, x = res[t]
-            assert st == rep_a["status"]
+            assert st == rep_a["status"] == ddg.DDG_OK
             assert rep["iterations"] == rep_a["iterations"]
             assert np.array_equal(x, x_a)
+            # the oracle's own assembly of the request judges the served solution
+            P = fem.assemble(mesh.xy, mesh.tri, coeffs=r)
+            tr = ddm.true_relative_residual(P.A, P.b, x[P.free])
+            assert tr <= 1.01e-6 and abs(tr - rep["true_rel_residual"]) <= 1e-9, (kind, tr)
+            assert np.array_equal(x[P.dirichlet], P.g[P.dirichlet])
+            if kind == ddg.DDG_DDM_GNN and mesh.n <= 20000:
+                # and the solution itself: within kappa * tol of the oracle's 1e-12 DDM-LU solve (reading C-19)
+                K = max(1, int(P.n_free / 1000 + 0.5))
+                asm = ddm.TwoLevelASM(P, pt.decompose(P, K, 2))
+                xs, _, _ = ddm.pcg(P.A, P.b, asm.apply_lu, 1e-12, 1000)
+                kappa = ddm.condition_estimate(P.A, lambda v: ddm.pcg(P.A, v, asm.apply_lu, 1e-6, 1000)[0], iters=3)
+                assert np.linalg.norm(x[P.free] - xs) <= kappa * (tr + 1e-12) * np.linalg.norm(xs)
         stats = ddg.ddg_serve_stats(ctx)
         assert stats["completed"] == len(reqs) and stats["pending"] == 0 and stats["active"] == 0
         assert stats["p99_ms"] >= stats["p50_ms"] > 0

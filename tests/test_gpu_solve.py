@@ -1,10 +1,15 @@
 """GPU flexible CG against the oracle's Krylov drivers (Algorithm 1; flexible CG)."""
+import os
+
 import numpy as np
 import pytest
 
 import synth
 from oracle import ddm
-from helpers import gpu_setup, oracle_setup
+from helpers import assert_close, gpu_setup, oracle_setup
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +37,7 @@ def test_unpreconditioned_cg_matches_oracle(ddg, ctx):
         rep, x = ddg.ddg_fcg_solve(p, 1e-8, 2000, 1)
         assert rep["status"] == 0
         assert abs(rep["iterations"] - it_ref) <= 1
-        assert ddm.true_relative_residual(P.A, P.b, x[P.free]) < 1.2e-8
+        assert ddm.true_relative_residual(P.A, P.b, x[P.free]) <= 1.01e-8
         assert np.array_equal(x[P.dirichlet], P.g[P.dirichlet])
     finally:
         ddg.ddg_problem_destroy(p)
@@ -52,7 +57,7 @@ def test_ddm_lu_pcg_small_config(ddg, ctx, m_trunc):
         assert rep["status"] == 0
         assert abs(rep["iterations"] - it_ref) <= 1
         tr = ddm.true_relative_residual(P.A, P.b, x[P.free])
-        assert tr < 1.2e-8 and abs(tr - rep["true_rel_residual"]) < 1e-10
+        assert tr <= 1.01e-8 and abs(tr - rep["true_rel_residual"]) < 1e-10
         u_ref = P.full_solution(np.linalg.solve(P.A.toarray(), P.b))
         assert np.max(np.abs(x - u_ref)) < 1e-6 * np.abs(u_ref).max()
     finally:
@@ -69,7 +74,7 @@ def test_ddm_lu_fcg_star(ddg, ctx):
         ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE)
         rep, x = ddg.ddg_fcg_solve(p, 1e-6, 500, 10)
         assert rep["status"] == 0 and abs(rep["iterations"] - it_ref) <= 1
-        assert ddm.true_relative_residual(P.A, P.b, x[P.free]) < 1.2e-6
+        assert ddm.true_relative_residual(P.A, P.b, x[P.free]) <= 1.01e-6
     finally:
         ddg.ddg_problem_destroy(p)
 
@@ -131,35 +136,64 @@ def test_failures_are_status_codes(ddg, ctx):
         ddg.ddg_problem_destroy(p)
 
 
-@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
-def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, schedule, monkeypatch):
-    """Both GNN schedules give the same local corrections; the CUDA-graph replay of the FCG
-    period gives the same iterates as direct launches."""
+def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, monkeypatch):
+    """Every GNN schedule gives the same local corrections as schedule 0 (element-wise), and
+    for every schedule the CUDA-graph replay of the FCG period gives the same iterates as
+    direct launches."""
     import torch
     w = synth.workload("star20000", 3)
     W = synth.dss_weights(30, 10, 3, bias_scale=0.1)
     p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, w.K, 2)
     m = ddg.ddg_model_create(ctx, 30, 10, 0.02, W)
+    ref = None
     try:
-        monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
-        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
-        info = ddg.ddg_problem_info(p)
-        r = torch.as_tensor(synth.residual_vector(info["n_free"], 5)).cuda()
-        corr = torch.zeros(info["sum_k"], dtype=torch.float64, device="cuda")
-        s = torch.zeros(info["K"], dtype=torch.float64, device="cuda")
-        ddg.ddg_local_corrections(p, r, corr, s)
-        torch.cuda.synchronize()
-        if schedule == "0":
-            test_gnn_schedules_agree_and_graph_replay_matches_direct.ref = corr.cpu().numpy()
-        else:
-            ref = test_gnn_schedules_agree_and_graph_replay_matches_direct.ref
+        for schedule in ["0", "1", "2", "3"]:
+            monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
+            monkeypatch.delenv("DDG_NO_GRAPH", raising=False)
+            ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+            info = ddg.ddg_problem_info(p)
+            r = torch.as_tensor(synth.residual_vector(info["n_free"], 5)).cuda()
+            corr = torch.zeros(info["sum_k"], dtype=torch.float64, device="cuda")
+            s = torch.zeros(info["K"], dtype=torch.float64, device="cuda")
+            ddg.ddg_local_corrections(p, r, corr, s)
+            torch.cuda.synchronize()
             got = corr.cpu().numpy()
-            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), schedule
-        r1, x1 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
-        monkeypatch.setenv("DDG_NO_GRAPH", "1")
-        r2, x2 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
-        assert r1["iterations"] == r2["iterations"] and np.array_equal(x1, x2)
-        assert r1["gnn_schedule"] == int(schedule)
+            if ref is None:
+                ref = got
+            else:
+                assert_close(got, ref, 1e-5, schedule)
+            r1, x1 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
+            monkeypatch.setenv("DDG_NO_GRAPH", "1")
+            r2, x2 = ddg.ddg_fcg_solve(p, 1e-6, 45, 10)
+            assert r1["iterations"] == r2["iterations"] and np.array_equal(x1, x2), schedule
+            assert r1["gnn_schedule"] == int(schedule)
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+@pytest.mark.parametrize("schedule", ["auto", "3"])
+def test_ddm_gnn_solve_judged_by_the_oracle(ddg, ctx, schedule, monkeypatch):
+    """DDM-GNN FCG(10) with the trained weights to 1e-6 on a ~20k-node star domain: the oracle's
+    own assembly gives the true relative residual, and x is within kappa * tol of the oracle's
+    1e-12 DDM-LU solve (reading C-19)."""
+    if schedule != "auto":
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
+    w = synth.workload("star20000", 7)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, w.K, 2)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, w.K, 2)
+    m = ddg.ddg_model_create(ctx, 30, 10, 1e-3, np.load(WEIGHTS).astype(np.float32))
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        rep, x = ddg.ddg_fcg_solve(p, 1e-6, 500, 10)
+        assert rep["status"] == ddg.DDG_OK, rep
+        tr = ddm.true_relative_residual(P.A, P.b, x[P.free])
+        assert tr <= 1.01e-6 and abs(tr - rep["true_rel_residual"]) <= 1e-9
+        assert np.array_equal(x[P.dirichlet], P.g[P.dirichlet])
+        asm = ddm.TwoLevelASM(P, Dd)
+        xs, _, _ = ddm.pcg(P.A, P.b, asm.apply_lu, 1e-12, 1000)
+        kappa = ddm.condition_estimate(P.A, lambda v: ddm.pcg(P.A, v, asm.apply_lu, 1e-6, 1000)[0], iters=3)
+        assert np.linalg.norm(x[P.free] - xs) <= kappa * (tr + 1e-12) * np.linalg.norm(xs)
     finally:
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)

@@ -114,3 +114,16 @@ def test_overlap_and_coarse_space_reduce_iterations():
     one = ddm.pcg(P.A, P.b, ddm.TwoLevelASM(P, D, coarse=False).apply_lu, 1e-6, 500)[1]
     two = ddm.pcg(P.A, P.b, ddm.TwoLevelASM(P, D).apply_lu, 1e-6, 500)[1]
     assert two < one
+
+
+def test_condition_estimate_bounds_the_dense_condition_number():
+    """The estimate against the dense eigenvalues of a small A_ff: at least the true condition
+    number up to the inverse iteration's error (1e-6 here: the two smallest eigenvalues of
+    the Dirichlet Laplacian are well apart), and within the factor the Gershgorin bound allows
+    (at most 2 for these meshes, whose largest eigenvalue is at least half the largest row sum)."""
+    w = synth.workload("square2k", 3)
+    P = fem.assemble(w.mesh.xy, w.mesh.tri, coeffs=w.coeffs)
+    ev = np.linalg.eigvalsh(P.A.toarray())
+    kappa = ev[-1] / ev[0]
+    est = ddm.condition_estimate(P.A)
+    assert kappa * (1 - 1e-6) <= est <= 2.0 * kappa, (kappa, est)

@@ -125,3 +125,45 @@ def test_dirichlet_lifting_matches_full_system():
     b[D] = P.g[D]
     u_full = np.linalg.solve(A, b)
     assert np.max(np.abs(u_full - solve(P))) < 1e-10
+
+
+def test_element_load_nodal_matches_symbolic_integral_of_the_interpolant():
+    """int_T f_h lambda_i with f_h the P1 interpolant of arbitrary nodal values, integrated
+    symbolically; a wrong mass weight (e.g. f_i + f_j + f_l in place of 2 f_i + f_j + f_l) fails."""
+    s, t = sympy.symbols("s t")
+    verts = [(sympy.Rational(1, 10), sympy.Rational(2, 10)), (sympy.Rational(9, 10), sympy.Rational(3, 10)),
+             (sympy.Rational(4, 10), sympy.Rational(8, 10))]
+    fv = [sympy.Rational(3, 2), sympy.Rational(-7, 3), sympy.Rational(5, 4)]
+    (x0, y0), (x1, y1), (x2, y2) = verts
+    jac = abs((x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0))
+    lam = [1 - s - t, s, t]
+    fh = sum(fv[k] * lam[k] for k in range(3))
+    exact = [float(sympy.integrate(sympy.integrate(fh * lam[i] * jac, (t, 0, 1 - s)), (s, 0, 1))) for i in range(3)]
+    xy = np.array([[float(a), float(b)] for a, b in verts])
+    got = fem.element_load_nodal(xy, np.array([[0, 1, 2]]), np.array([float(v) for v in fv]))[0]
+    assert np.allclose(got, exact, rtol=1e-14, atol=1e-15)
+
+
+def test_nodal_load_of_affine_f_is_exact_and_sums_to_the_integral():
+    """For affine f the P1 interpolant is f itself, so the consistent-mass load equals the exact
+    element integral (the quadratic rule, itself pinned symbolically above), and its total is
+    sum_T |T| (f_a + f_b + f_c) / 3 (the exact integral of an affine function over a triangle)."""
+    m = synth.star_mesh(2000, seed=8)
+    fun = lambda x, y: 2.5 - 1.25 * x + 0.75 * y
+    f = fun(m.xy[:, 0], m.xy[:, 1])
+    got = fem.element_load_nodal(m.xy, m.tri, f)
+    ref = fem.element_load_quadratic(m.xy, m.tri, fun)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
+    _, _, area = fem.triangle_geometry(m.xy, m.tri)
+    total = float(np.sum(area * f[m.tri].sum(axis=1) / 3.0))
+    assert abs(got.sum() - total) <= 1e-13 * abs(total)
+
+
+def test_quadratic_solution_with_nodal_forcing():
+    """The nodal-f path with f != 0: u = x^2 + y^2 + xy has -Lap(u) = -4, a constant, whose
+    consistent-mass load is exact; on the right-triangle grid the P1 solution is nodally exact."""
+    m = synth.square_mesh(17, jitter=0.0, diag="fixed")
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    u = x * x + y * y + x * y
+    P = fem.assemble(m.xy, m.tri, f_nodal=np.full(m.n, -4.0), g_nodal=u)
+    assert np.max(np.abs(solve(P) - u)) < 1e-12
