@@ -617,16 +617,15 @@ def _lu_solve_seconds(res, iterations):
 
 def oracle_lu_baseline(a, lu_iterations: int, replicas: int):
     """The oracle's DDM-LU PCG (the paper's CPU comparator, Table 3) on the same workload: one
-    single-threaded solve alone, then `replicas` independent single-threaded solves at once on
-    the host cores (seeds seed .. seed + replicas - 1), whose aggregate is solves/s on all cores."""
+    single-threaded solve alone, then `replicas` independent single-threaded solves of the same
+    problem at once on the host cores, whose aggregate is solves/s on all cores."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     reps = max(1, min(replicas, cores))
     pool = _one_thread_pool(reps)
     try:
         alone = pool.apply(_oracle_lu_solve, ((a.workload, a.seed, a.tol, a.cpu_seconds),))
         t0 = time.perf_counter()
-        many = pool.map(_oracle_lu_solve, [(a.workload, a.seed + k, a.tol, a.cpu_seconds) for k in range(reps)],
-                        chunksize=1)
+        many = pool.map(_oracle_lu_solve, [(a.workload, a.seed, a.tol, a.cpu_seconds)] * reps, chunksize=1)
         wall = time.perf_counter() - t0
     finally:
         pool.terminate()
@@ -644,8 +643,8 @@ def oracle_lu_baseline(a, lu_iterations: int, replicas: int):
             "value_1thread": 1.0 / t1, "solve_s_1thread": t1, "iterations": it1,
             "setup_s_1thread": alone["t_setup_s"], "extrapolated": sampled,
             "wall_s_all_cores": wall, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
-            "sample": f"{a.workload}: {what}; 1 thread alone, then {reps} single-threaded solves of seeds "
-                      f"{a.seed}..{a.seed + reps - 1} at once (all-core value = {reps} / slowest)"}
+            "sample": f"{a.workload}: {what}; 1 thread alone, then {reps} single-threaded solves of the same "
+                      f"problem at once (all-core value = {reps} / slowest)"}
 
 
 def _oracle_dss(job):
