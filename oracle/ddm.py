@@ -95,7 +95,7 @@ class DDMGNN:
 
 def pcg(A, b: np.ndarray, M, tol: float, max_iter: int):
     """Algorithm 1 with u_0 = 0; returns (u, iterations, history of |r|/|b|).
-    b = 0 returns u = 0 after zero iterations (reading C-20: |r|/|b| is undefined there)."""
+    b = 0 returns u = 0 after zero iterations (reading C-21: |r|/|b| is undefined there)."""
     u = np.zeros_like(b)
     r = b.copy()
     bn = np.linalg.norm(b)
@@ -123,7 +123,7 @@ def pcg(A, b: np.ndarray, M, tol: float, max_iter: int):
 
 def fcg(A, b: np.ndarray, M, tol: float, max_iter: int, m: int):
     """Flexible CG with truncation m and u_0 = 0; returns (u, iterations, history of |r|/|b|).
-    b = 0 returns u = 0 after zero iterations (reading C-20)."""
+    b = 0 returns u = 0 after zero iterations (reading C-21)."""
     u = np.zeros_like(b)
     r = b.copy()
     bn = np.linalg.norm(b)

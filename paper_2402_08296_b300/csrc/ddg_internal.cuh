@@ -124,6 +124,7 @@ struct ddg_model {
     size_t packed_per_block = 0;
     std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
     std::vector<float> fused_host;   // composed per-block layout of the fused GNN kernel (kernel parameters)
+    float *tc_w = nullptr;           // per-block tensor-core weight images of schedule 4 (device)
     float *adam_m = nullptr, *adam_v = nullptr;  // Adam moments, kept across training calls
     long long adam_t = 0;
     ddg::Allocs allocs;
@@ -133,8 +134,9 @@ struct ddg_model {
 struct ChunkPlan {
     int T = 0, nchunks = 0, max_need = 0;
     size_t max_smem = 0;  // schedule 3: largest per-CTA shared memory of the plan
-    bool global = false;  // schedule 3: chunks are ranges of the concatenated graphs' nodes, sized to fill
+    bool global = false;  // schedules 3, 4: chunks are ranges of the concatenated graphs' nodes, sized to fill
                           // the GPU evenly; own nodes sorted by message count, neighbour kind in bit 15
+    bool tc = false;      // schedule 4: at most T own and TC_NEED needed nodes per chunk (tensor-core kernel)
     int *gid = nullptr;   // global: graph of every local node (sum_loc)
     int4 *info = nullptr; // global: per own slot {node, corr index or -1, free index of r or -1,
                           //   graph | out-messages << 24}
@@ -209,10 +211,12 @@ struct ddg_problem {
     // GNN weights in use: the model's, or (DDG_BF16_WEIGHTS) this problem's copies rounded to bfloat16
     bool w_bf16 = false;
     float *bf16_packed_dev = nullptr;
+    float *bf16_tc_dev = nullptr;   // schedule-4 weight images of the rounded weights
     std::vector<float> bf16_packed_host, bf16_fused_host;
     bool dss_whole_graph = true;  // every local graph fits one CTA (schedules 0 and 1 allowed)
     int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block,
-                                // 3 chunked per block with composed weights and packed two-lane FP32
+                                // 3 chunked per block with composed weights and packed two-lane FP32,
+                                // 4 as 3 with the per-node matrix products on the tensor cores
     float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedules 1, 2)
     float *dss_h2 = nullptr;    // second latent buffer (schedule 2)
     ChunkPlan chunk;
@@ -300,10 +304,18 @@ int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaSt
 int32_t dss_check_capacity(ddg_problem *p);
 int32_t dss_autotune(ddg_problem *p);
 int32_t chunk_build(ddg_problem *p, int T);
-int32_t chunk_build_global(ddg_problem *p, int T);
+struct ChunkArgs;
+int32_t chunk_build_global(ddg_problem *p, int T, bool tc);
+// schedule 4 (dss_tc.cu): per-node matrix products of the GNN on the tensor cores
+constexpr int TC_T = 256;            // threads of a CTA, and own nodes of a chunk at most
+constexpr int TC_NEED = 384;         // needed nodes of a chunk at most (three 128-row tiles)
+constexpr int TCW_FLOATS = 3328;     // floats of one block's tensor-core weight image
+constexpr size_t TC_SMEM = 96512;    // dynamic shared memory of a schedule-4 CTA (at most two per SM)
+void tc_weight_image(const float *fused, int kbar, std::vector<float> &img);
+int32_t tc_ctas_per_sm(int *out);
+int32_t dss_tc_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *tc_w, cudaStream_t s);
 // fused GNN steps over several problems (request loop): schedule 3 with chunk width GROUP_T
 constexpr int GROUP_T = 128;
-struct ChunkArgs;
 int32_t dss_group_prepare(ddg_problem *p);
 bool dss_group_compatible(const ddg_problem *a, const ddg_problem *b);
 size_t dss_group_args_bytes();

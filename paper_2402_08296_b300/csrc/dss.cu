@@ -167,6 +167,11 @@ int32_t model_host_layouts(ddg_model *m) {
     std::vector<float> flat(m->n_w);
     DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
     host_layouts(flat, m->kbar, m->d, m->alpha, m->packed_host, m->fused_host);
+    // schedule 4's weight images, rebuilt with the layouts so that retrained weights are seen
+    std::vector<float> img;
+    tc_weight_image(m->fused_host.data(), m->kbar, img);
+    if (!m->tc_w) DDG_TRY(dalloc(m->ctx, m->allocs, &m->tc_w, img.size()));
+    DDG_CU(cudaMemcpy(m->tc_w, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
     return DDG_OK;
 }
 
@@ -203,6 +208,7 @@ int32_t dss_select_weights(ddg_problem *p, bool bf16) {
     const ddg_model *m = p->model;
     p->w_bf16 = bf16;
     p->bf16_packed_dev = nullptr;
+    p->bf16_tc_dev = nullptr;
     if (!bf16) return DDG_OK;
     std::vector<float> flat(m->n_w);
     DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
@@ -213,6 +219,12 @@ int32_t dss_select_weights(ddg_problem *p, bool bf16) {
     DDG_CU(cudaMemcpy(dev, p->bf16_packed_host.data(), sizeof(float) * p->bf16_packed_host.size(),
                       cudaMemcpyHostToDevice));
     p->bf16_packed_dev = dev;
+    std::vector<float> img;
+    tc_weight_image(p->bf16_fused_host.data(), m->kbar, img);
+    float *tdev = nullptr;
+    DDG_TRY(dalloc(p->ctx, p->a_pre, &tdev, img.size()));
+    DDG_CU(cudaMemcpy(tdev, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
+    p->bf16_tc_dev = tdev;
     return DDG_OK;
 }
 
@@ -648,28 +660,6 @@ __global__ void __launch_bounds__(DSS_THREADS, 1) k_dss_step(const __grid_consta
 // receives work even when there are fewer graphs than SMs.  Latents alternate
 // between two global buffers, because a chunk reads the latents of nodes that
 // other chunks update in the same launch.
-struct ChunkArgs {
-    const int *c_graph, *c_n0, *c_own;      // per chunk: graph, first own node (graph-local), own count
-    const int *c_need_off, *c_need_n;       // per chunk: start / count of its needed-node list
-    const int *need;                        // graph-local ids: own nodes first, then outside neighbours
-    const int *c_adj_off;                   // per chunk: start of its own nodes' CSR in adj_ptr
-    const int *adj_ptr;                     // own-node CSR offsets (relative to the chunk's adj start)
-    const uint16_t *adj;                    // chunk-local neighbour ids
-    const int *c_adj_base;                  // per chunk: start of its slice in adj
-    const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
-    const int *gid;                         // global plans: graph of every local node
-    const int4 *info;                       // global plans: per own slot {node, corr idx, r idx, graph | dout << 24}
-    const float2 *loc_xy;
-    const double *r, *s;
-    double *corr;
-    const float *h_in;                      // [D][n_total]
-    float *h_out;                           // [D][n_total]
-    float *c;                               // [n_total]
-    long long n_total;
-    float alpha;
-    int first, last;
-    const int *stop;
-};
 
 template <int T>
 __global__ void __launch_bounds__(T, 65536 / (T * 112)) k_dss_chunk(const __grid_constant__ BlockWeights W,
@@ -834,39 +824,6 @@ __device__ __forceinline__ void fused_project(const FusedWeights &W, const float
         f2_unpack(acc[2 * m], a0, a1);
         f2_unpack(acc[2 * m + 1], b0, b1);
         dst[m] = make_float4(a0, a1, b0, b1);
-    }
-}
-
-// h (10 floats) and c of a local node from its 12-float latent row
-__device__ __forceinline__ void load_hrow(const float4 *rows, int node, float (&h)[D], float &c) {
-    const float4 r0 = rows[3 * (size_t)node], r1 = rows[3 * (size_t)node + 1], r2 = rows[3 * (size_t)node + 2];
-    h[0] = r0.x; h[1] = r0.y; h[2] = r0.z; h[3] = r0.w;
-    h[4] = r1.x; h[5] = r1.y; h[6] = r1.z; h[7] = r1.w;
-    h[8] = r2.x; h[9] = r2.y;
-    c = r2.z;
-}
-
-// acc[m] += sum_i W[OFF + i*STRIDE + 2m .. 2m+1] x_i  over i < D (pairs of outputs)
-template <int OFF, int STRIDE>
-__device__ __forceinline__ void f2_mv(f2_t (&acc)[D / 2], const f2_t *Wp, const float (&x)[D]) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const f2_t xi = f2_pack(x[i], x[i]);
-#pragma unroll
-        for (int m = 0; m < D / 2; ++m) acc[m] = f2_fma(Wp[(OFF + i * STRIDE) / 2 + m], xi, acc[m]);
-    }
-}
-
-// one message pair-block with the position terms already in pa and pb:
-// acc += mask * relu(pa + pb + We_|d| |d|)
-template <int OFF_WE, bool MASKED>
-__device__ __forceinline__ void f2_msg_n(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 2], const f2_t (&pb)[D / 2],
-                                         const f2_t *Wp, f2_t dn2, f2_t mask2) {
-#pragma unroll
-    for (int m = 0; m < D / 2; ++m) {
-        f2_t z = f2_add(pa[m], pb[m]);
-        z = f2_fma(Wp[(OFF_WE + 2 * D) / 2 + m], dn2, z);
-        acc[m] = MASKED ? f2_fma(f2_relu(z), mask2, acc[m]) : f2_add(acc[m], f2_relu(z));
     }
 }
 
@@ -1367,6 +1324,7 @@ void chunk_free(ddg_problem *p) {
     p->chunk.gid = nullptr;
     p->chunk.info = nullptr;
     p->chunk.global = false;
+    p->chunk.tc = false;
     (void)empty;
 }
 
@@ -1482,10 +1440,13 @@ static int32_t fused_ctas_per_sm(size_t smem, int *out) {
     return DDG_OK;
 }
 
-// Global chunk plan of schedule 3: the concatenated graphs' nodes cut into
-// equal ranges, as many as fill every SM's resident CTAs a whole number of
-// times (at most 2T nodes each), so every SM gets the same work per block.
-int32_t chunk_build_global(ddg_problem *p, int T) {
+// Global chunk plan of schedules 3 and 4: the concatenated graphs' nodes cut into
+// equal-work ranges, as many as fill every SM's resident CTAs a whole number of
+// times, so every SM gets the same work per block.  Schedule 3 (tc = false) takes
+// at most 2T own nodes per chunk; schedule 4 (tc = true) at most T own nodes and
+// TC_NEED needed nodes (own plus outside neighbours), splitting any range whose
+// needed nodes exceed that in two until none does.
+int32_t chunk_build_global(ddg_problem *p, int T, bool tc) {
     ddg_ctx *c = p->ctx;
     cudaStream_t s = p->stream;
     chunk_free(p);
@@ -1494,17 +1455,26 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     const int K = p->K;
     int sms = 0, per_sm = 0;
     DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t smem_est = fused_smem(3 * T, 2 * T);  // 2T own + T outside nodes
-    switch (T) {
-        case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
-        case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
-        default: set_error("schedule-3 chunk width must be 128 or 256"); return DDG_INVALID_ARG;
+    const long long own_cap = tc ? T : 2LL * T;
+    if (tc) {
+        if (T != TC_T) {
+            set_error("schedule-4 chunk width must be 256");
+            return DDG_INVALID_ARG;
+        }
+        DDG_TRY(tc_ctas_per_sm(&per_sm));
+    } else {
+        const size_t smem_est = fused_smem(3 * T, 2 * T);  // 2T own + T outside nodes
+        switch (T) {
+            case 128: DDG_TRY(fused_ctas_per_sm<128>(smem_est, &per_sm)); break;
+            case 256: DDG_TRY(fused_ctas_per_sm<256>(smem_est, &per_sm)); break;
+            default: set_error("schedule-3 chunk width must be 128 or 256"); return DDG_INVALID_ARG;
+        }
     }
     const long long slots = (long long)sms * std::max(1, per_sm);
-    const long long waves = std::max(1LL, (n + slots * 2 * T - 1) / (slots * 2 * T));
-    // at least one node per thread: a small problem takes fewer CTAs (and leaves SMs to the
-    // kernels of other streams) rather than slivers of a few nodes with large halos
-    const long long cs = std::max<long long>(T, (n + slots * waves - 1) / (slots * waves));
+    const long long waves = std::max(1LL, (n + slots * own_cap - 1) / (slots * own_cap));
+    // at least half the cap: a small problem takes fewer CTAs (and leaves SMs to the kernels of
+    // other streams) rather than slivers of a few nodes with large halos
+    const long long cs = std::max<long long>(own_cap / 2, (n + slots * waves - 1) / (slots * waves));
     const long long nc_target = (n + cs - 1) / cs;
     std::vector<int> lp(K + 1), lk(K), nptr(n + K), gid(n), cn0, cown;
     DDG_CU(cudaMemcpyAsync(lp.data(), p->loc_ptr, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
@@ -1523,24 +1493,74 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
             work[u] = 500.0 + (j < lk[g] ? 95.0 : 60.0) * deg;
             total += work[u];
         }
-    // equal-work ranges (at most 2T nodes each), about nc_target of them
+    // equal-work ranges (at most own_cap nodes each), about nc_target of them
     const double per = total / (double)nc_target;
     double acc = 0.0;
     long long start = 0;
     for (long long u = 0; u < n; ++u) {
         acc += work[u];
         const long long len = u + 1 - start;
-        if (len == 2LL * T || acc >= per * (double)(cn0.size() + 1) || u == n - 1) {
+        if (len == own_cap || acc >= per * (double)(cn0.size() + 1) || u == n - 1) {
             cn0.push_back((int)start);
             cown.push_back((int)len);
             start = u + 1;
         }
     }
+    DDG_TRY(dalloc(c, cp.allocs, &cp.gid, n));
+    DDG_CU(cudaMemcpyAsync(cp.gid, gid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    // pass 0: needed nodes and adjacency entries per chunk (schedule 4: split the ranges whose
+    // needed nodes exceed the cap, and count again)
+    std::vector<int> hn, ha;
+    Scratch sc(s);
+    for (int round = 0;; ++round) {
+        const int nc = (int)cn0.size();
+        int *t_n0 = nullptr, *t_own = nullptr, *t_need = nullptr, *t_adj = nullptr;
+        DDG_CU(sc.get(&t_n0, nc));
+        DDG_CU(sc.get(&t_own, nc));
+        DDG_CU(sc.get(&t_need, nc));
+        DDG_CU(sc.get(&t_adj, nc));
+        DDG_CU(cudaMemcpyAsync(t_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+        DDG_CU(cudaMemcpyAsync(t_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+        k_gchunk_build<<<nc, 256, 0, s>>>(t_n0, t_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
+                                          p->nbr, p->sub_ptr, p->sub_idx, 0, t_need, t_adj, nullptr, nullptr,
+                                          nullptr, nullptr, nullptr, nullptr, nullptr, p->d_status);
+        DDG_LAUNCH_CHECK();
+        hn.assign(nc, 0);
+        ha.assign(nc, 0);
+        DDG_CU(cudaMemcpyAsync(hn.data(), t_need, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+        DDG_CU(cudaMemcpyAsync(ha.data(), t_adj, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+        DDG_CU(cudaStreamSynchronize(s));
+        DDG_TRY(check_status(p, "GNN chunks"));
+        for (void *q : {(void *)t_n0, (void *)t_own, (void *)t_need, (void *)t_adj}) DDG_CU(sc.drop(q));
+        if (!tc) break;
+        std::vector<int> n0b, ownb;
+        bool split = false;
+        for (int q = 0; q < nc; ++q) {
+            if (hn[q] > TC_NEED && cown[q] > 1) {
+                const int h1 = cown[q] / 2;
+                n0b.push_back(cn0[q]);
+                ownb.push_back(h1);
+                n0b.push_back(cn0[q] + h1);
+                ownb.push_back(cown[q] - h1);
+                split = true;
+            } else {
+                n0b.push_back(cn0[q]);
+                ownb.push_back(cown[q]);
+            }
+        }
+        if (!split) break;
+        if (round == 8) {
+            set_error("a schedule-4 GNN chunk keeps more needed nodes than a CTA holds");
+            return DDG_TOO_LARGE;
+        }
+        cn0.swap(n0b);
+        cown.swap(ownb);
+    }
     const int nc = (int)cn0.size();
     cp.T = T;
     cp.global = true;
+    cp.tc = tc;
     cp.nchunks = nc;
-    DDG_TRY(dalloc(c, cp.allocs, &cp.gid, n));
     DDG_TRY(dalloc(c, cp.allocs, &cp.info, n));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_n0, nc));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_own, nc));
@@ -1548,21 +1568,9 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_need_n, nc));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_off, nc));
     DDG_TRY(dalloc(c, cp.allocs, &cp.c_adj_base, nc));
-    DDG_CU(cudaMemcpyAsync(cp.gid, gid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_n0, cn0.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-    Scratch sc(s);
-    int *adj_n = nullptr;
-    DDG_CU(sc.get(&adj_n, nc));
-    k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
-                                      p->nbr, p->sub_ptr, p->sub_idx, 0, cp.c_need_n, adj_n, nullptr, nullptr,
-                                      nullptr, nullptr, nullptr, nullptr, nullptr, p->d_status);
-    DDG_LAUNCH_CHECK();
-    std::vector<int> hn(nc), ha(nc);
-    DDG_CU(cudaMemcpyAsync(hn.data(), cp.c_need_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
-    DDG_CU(cudaMemcpyAsync(ha.data(), adj_n, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
-    DDG_CU(cudaStreamSynchronize(s));
-    DDG_TRY(check_status(p, "GNN chunks"));
+    DDG_CU(cudaMemcpyAsync(cp.c_need_n, hn.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     std::vector<int> noff(nc), aoff(nc), abase(nc);
     long long tn = 0, ta = 0, tp = 0;
     int maxn = 0;
@@ -1575,7 +1583,7 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
         ta += ha[q];
         tp += cown[q] + 1;
         maxn = std::max(maxn, hn[q]);
-        max_smem = std::max(max_smem, fused_smem(hn[q], cown[q]));
+        max_smem = std::max(max_smem, tc ? (size_t)TC_SMEM : fused_smem(hn[q], cown[q]));
     }
     cp.max_need = maxn;
     cp.max_smem = max_smem;
@@ -1593,7 +1601,6 @@ int32_t chunk_build_global(ddg_problem *p, int T) {
                                       p->nbr, p->sub_ptr, p->sub_idx, 1, nullptr, nullptr, cp.c_need_off, cp.need,
                                       cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->d_status);
     DDG_LAUNCH_CHECK();
-    DDG_CU(sc.drop(adj_n));
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
 }
@@ -1655,6 +1662,7 @@ static ChunkArgs chunk_args(ddg_problem *p, const double *r, const int *stop) {
     a.n_total = p->sum_loc;
     a.alpha = p->model->alpha;
     a.stop = stop;
+    a.status = p->d_status;
     a.h_in = p->dss_h;
     a.h_out = p->dss_h2;
     return a;
@@ -1663,6 +1671,7 @@ static ChunkArgs chunk_args(ddg_problem *p, const double *r, const int *stop) {
 int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     const ChunkPlan &cp = p->chunk;
     const ChunkArgs a = chunk_args(p, r, stop);
+    if (cp.tc) return dss_tc_launch(p, a, w_fused_host(p), p->w_bf16 ? p->bf16_tc_dev : p->model->tc_w, s);
     if (cp.global) {
         switch (cp.T) {
             case 128: return launch_fused<128>(p, a, s);
@@ -1721,8 +1730,8 @@ bool dss_group_compatible(const ddg_problem *a, const ddg_problem *b) {
 
 int32_t dss_group_prepare(ddg_problem *p) {
     if (p->kind != DDG_DDM_GNN) return DDG_INVALID_ARG;
-    if (p->dss_sched != 3 || p->chunk.T != GROUP_T || !p->chunk.global) {
-        DDG_TRY(chunk_build_global(p, GROUP_T));
+    if (p->dss_sched != 3 || p->chunk.T != GROUP_T || !p->chunk.global || p->chunk.tc) {
+        DDG_TRY(chunk_build_global(p, GROUP_T, false));
         p->dss_sched = 3;
     }
     return DDG_OK;
@@ -1830,7 +1839,7 @@ int32_t dss_step_launch(ddg_problem *p, const double *r, const int *stop, cudaSt
 
 int32_t dss_launch_args(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     if (p->dss_sched == 1) return dss_step_launch(p, r, stop, s);
-    if (p->dss_sched == 2 || p->dss_sched == 3) return dss_chunk_launch(p, r, stop, s);
+    if (p->dss_sched >= 2) return dss_chunk_launch(p, r, stop, s);
     const ddg_model *m = p->model;
     DssArgs a;
     a.weights = w_packed_dev(p);

@@ -200,4 +200,63 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
+
+// ---------------------------------------------------------------- chunked schedules (2, 3, 4)
+struct ChunkArgs {
+    const int *c_graph, *c_n0, *c_own;      // per chunk: graph, first own node (graph-local), own count
+    const int *c_need_off, *c_need_n;       // per chunk: start / count of its needed-node list
+    const int *need;                        // graph-local ids: own nodes first, then outside neighbours
+    const int *c_adj_off;                   // per chunk: start of its own nodes' CSR in adj_ptr
+    const int *adj_ptr;                     // own-node CSR offsets (relative to the chunk's adj start)
+    const uint16_t *adj;                    // chunk-local neighbour ids
+    const int *c_adj_base;                  // per chunk: start of its slice in adj
+    const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
+    const int *gid;                         // global plans: graph of every local node
+    const int4 *info;                       // global plans: per own slot {node, corr idx, r idx, graph | dout << 24}
+    const float2 *loc_xy;
+    const double *r, *s;
+    double *corr;
+    const float *h_in;                      // [D][n_total]
+    float *h_out;                           // [D][n_total]
+    float *c;                               // [n_total]
+    long long n_total;
+    float alpha;
+    int first, last;
+    const int *stop;
+    int *status;                            // device status word (bits ST_*)
+};
+
+// h (10 floats) and c of a local node from its 12-float latent row
+__device__ __forceinline__ void load_hrow(const float4 *rows, int node, float (&h)[D], float &c) {
+    const float4 r0 = rows[3 * (size_t)node], r1 = rows[3 * (size_t)node + 1], r2 = rows[3 * (size_t)node + 2];
+    h[0] = r0.x; h[1] = r0.y; h[2] = r0.z; h[3] = r0.w;
+    h[4] = r1.x; h[5] = r1.y; h[6] = r1.z; h[7] = r1.w;
+    h[8] = r2.x; h[9] = r2.y;
+    c = r2.z;
+}
+
+// acc[m] += sum_i W[OFF + i*STRIDE + 2m .. 2m+1] x_i  over i < D (pairs of outputs)
+template <int OFF, int STRIDE>
+__device__ __forceinline__ void f2_mv(f2_t (&acc)[D / 2], const f2_t *Wp, const float (&x)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const f2_t xi = f2_pack(x[i], x[i]);
+#pragma unroll
+        for (int m = 0; m < D / 2; ++m) acc[m] = f2_fma(Wp[(OFF + i * STRIDE) / 2 + m], xi, acc[m]);
+    }
+}
+
+// one message pair-block with the position terms already in pa and pb:
+// acc += mask * relu(pa + pb + We_|d| |d|)
+template <int OFF_WE, bool MASKED>
+__device__ __forceinline__ void f2_msg_n(f2_t (&acc)[D / 2], const f2_t (&pa)[D / 2], const f2_t (&pb)[D / 2],
+                                         const f2_t *Wp, f2_t dn2, f2_t mask2) {
+#pragma unroll
+    for (int m = 0; m < D / 2; ++m) {
+        f2_t z = f2_add(pa[m], pb[m]);
+        z = f2_fma(Wp[(OFF_WE + 2 * D) / 2 + m], dn2, z);
+        acc[m] = MASKED ? f2_fma(f2_relu(z), mask2, acc[m]) : f2_add(acc[m], f2_relu(z));
+    }
+}
+
 }  // namespace ddg

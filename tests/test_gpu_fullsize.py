@@ -87,6 +87,25 @@ def test_full_matrix_and_partition(ddg, full):
     assert info["max_loc"] <= 2048
 
 
+def test_full_coarse_matrix_and_inverse(ddg, torch, full):
+    """The coarse level at full size (Eq. 7's R_0 A R_0^T, K ~ 100 and ~ 1,000): A_0 against the
+    oracle's Z^T A Z, the set-up inverse against the identity, and the coarse term Z A_0^-1 Z^T r
+    it gives against the oracle's Cholesky solve.  The GPU's own application of the term is
+    checked inside the whole DDM-LU preconditioner by test_full_ddm_lu."""
+    name, w, P, D, p = full
+    A0, A0inv = ddg.ddg_coarse_download(p)
+    K = A0.shape[0]
+    assert np.max(np.abs(A0 - D.A0)) <= 1e-12 * np.abs(D.A0).max()
+    assert np.array_equal(A0, A0.T)
+    assert np.max(np.abs(A0inv @ D.A0 - np.eye(K))) < 1e-8
+    import scipy.linalg as sla
+    r = synth.residual_vector(P.n_free, 80)
+    y = D.Z.T @ r
+    ref = D.Z @ sla.cho_solve(sla.cho_factor(D.A0, lower=True), y)
+    got = D.Z @ (A0inv @ y)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.abs(ref).max()
+
+
 def _sample(D, count=4):
     sizes = np.array([len(S) for S in D.sets])
     pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
@@ -96,8 +115,13 @@ def _sample(D, count=4):
     return sorted(pick)
 
 
-def test_full_gnn_corrections_sampled(ddg, ctx, torch, full):
+@pytest.mark.parametrize("schedule", ["auto", "3", "4"])
+def test_full_gnn_corrections_sampled(ddg, ctx, torch, full, schedule, monkeypatch):
+    """Sampled subdomains' GNN corrections at the full sizes: the schedule the autotuner picks
+    (the benchmark's launch configuration) and the two chunked schedules explicitly."""
     name, w, P, D, p = full
+    if schedule != "auto":
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
     W = bench_weights()
     m = ddg.ddg_model_create(ctx, KBAR, DLAT, ALPHA, W)
     try:

@@ -68,7 +68,7 @@ def test_fcg_with_fixed_spd_preconditioner_matches_pcg(small):
 
 
 def test_zero_right_hand_side_has_the_zero_solution(small):
-    """A is SPD, so A u = 0 only for u = 0; both drivers return it without iterating (reading C-20)."""
+    """A is SPD, so A u = 0 only for u = 0; both drivers return it without iterating (reading C-21)."""
     P = small
     D = pt.decompose(P, 4, 1)
     asm = ddm.TwoLevelASM(P, D)
