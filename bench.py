@@ -446,6 +446,36 @@ def run_variants(a, local_rank):
                 rows.append({"precond": "DDM-GNN" if kbar else "DDM-LU", "kbar": kbar, "level": level, "N_s": ns,
                              "K": K, "overlap": delta, "tol": tol, "iterations": int(np.median(its)),
                              "true_rel_residual": float(np.max(res)), "ms": ms, "solves_per_s": 1e3 / ms})
+    # Table 2 / Fig. 6 grid: the batched GNN's application time for every (kbar, d), on the
+    # default decomposition (random weights: the time depends on the shape only; d != 10 runs
+    # on the generic schedule 5, d = 10 on the schedule the autotuner picks)
+    ddg.ddg_partition(p, max(1, int(round(n_free / 1000))), 2)
+    info = ddg.ddg_problem_info(p)
+    r_dev = torch.as_tensor(synth.residual_vector(n_free, 3)).cuda()
+    corr = torch.zeros(info["sum_k"], dtype=torch.float64, device="cuda")
+    s_dev = torch.zeros(info["K"], dtype=torch.float64, device="cuda")
+    grid = []
+    for kb in (5, 10, 20, 30):
+        for dd in (5, 10, 20):
+            mdl = ddg.ddg_model_create(ctx, kb, dd, ALPHA, None, seed=kb * 100 + dd)
+            try:
+                ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, mdl, ddg.DDG_COARSE)
+                for _ in range(2):
+                    ddg.ddg_local_corrections(p, r_dev, corr, s_dev)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                cur = torch.cuda.current_stream()
+                e0.record(cur)
+                for _ in range(10):
+                    ddg.ddg_local_corrections(p, r_dev, corr, s_dev)
+                e1.record(cur)
+                torch.cuda.synchronize()
+                rep, _ = ddg.ddg_fcg_solve(p, 1e-6, 1, a.m, want_x=False)  # reports the schedule in use
+                grid.append({"kbar": kb, "d": dd, "n_weights": kb * (11 * dd * dd + 15 * dd + 1),
+                             "application_ms": e0.elapsed_time(e1) / 10, "gnn_schedule": rep["gnn_schedule"]})
+            finally:
+                ddg.ddg_setup_precond(p, ddg.DDG_NONE)
+                ddg.ddg_model_destroy(mdl)
     for m, _ in models.values():
         ddg.ddg_model_destroy(m)
     ddg.ddg_problem_destroy(p)
@@ -456,7 +486,7 @@ def run_variants(a, local_rank):
             "vs_baseline": None, "dtype": "f32 GNN / f64 Krylov", "data": "synthetic",
             "config": {"workload": "variants", "mesh": base, "n_free": n_free, "fcg_m": a.m,
                        "weights": {str(k): v[1] for k, v in models.items()}},
-            "rows": rows}
+            "rows": rows, "kbar_d_grid": grid}
 
 
 # ---------------------------------------------------------------- serving

@@ -162,12 +162,15 @@ int32_t ddg_coarse_download(ddg_problem *p, double *A0, double *A0_inv);
 
 /* ---- DSS model (Section III-B; Table 2) -------------------------------- */
 
-/* Create a model with kbar blocks of latent size d (d = 10 is compiled) and
- * ResNet step alpha.  w (n_w = kbar * (11 d^2 + 15 d + 1) floats, layout per
- * block row-major W[out][in]: Phi_out W1[d][2d+3] b1[d] W2[d][d] b2[d];
- * Phi_in the same; Psi W1[d][3d+1] b1[d] W2[d][d] b2[d]; D W1[d][d] b1[d]
- * W2[1][d] b2[1]) or NULL for Xavier-uniform matrices and zero biases drawn
- * from SplitMix64(seed).  Errors: DDG_INVALID_ARG (n_w mismatch, d != 10). */
+/* Create a model with kbar blocks of latent size d and ResNet step alpha.
+ * d = 10 (the paper's setting) runs on every GNN schedule, the training
+ * kernels and BF16 weights; d = 5 and d = 20 (the other columns of Table 2's
+ * sweep) run inference on the generic schedule 5.  w (n_w = kbar * (11 d^2 +
+ * 15 d + 1) floats, layout per block row-major W[out][in]: Phi_out W1[d][2d+3]
+ * b1[d] W2[d][d] b2[d]; Phi_in the same; Psi W1[d][3d+1] b1[d] W2[d][d] b2[d];
+ * D W1[d][d] b1[d] W2[1][d] b2[1]) or NULL for Xavier-uniform matrices and
+ * zero biases drawn from SplitMix64(seed).  Errors: DDG_INVALID_ARG (n_w
+ * mismatch, d not in {5, 10, 20}). */
 int32_t ddg_model_create(ddg_ctx *ctx, int32_t kbar, int32_t d, float alpha, const float *w, size_t n_w,
                          uint64_t seed, ddg_model **out);
 int32_t ddg_model_destroy(ddg_model *m);
@@ -191,7 +194,8 @@ int32_t ddg_model_set_weights(ddg_model *m, const float *w, size_t n_w);
  * improvement.  The model's weights are updated in place; its Adam moments
  * persist in the model, so successive calls on different problems continue
  * one optimisation.  Errors:
- * DDG_INVALID_ARG (no partition, bad options), DDG_OOM, DDG_CUDA_ERROR. */
+ * DDG_INVALID_ARG (no partition, bad options, a model with d != 10), DDG_OOM,
+ * DDG_CUDA_ERROR. */
 typedef struct ddg_train_opts {
     int32_t steps;          /* optimiser steps */
     int32_t batch;          /* samples per step */
@@ -216,7 +220,7 @@ int32_t ddg_train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts
  * c = R_i r / |R_i r| from one device residual r_dev (n_free FP64): loss =
  * mean over graphs[0..nb) of sum_k mean((R_i A R_i^T r_hat^k - c)^2), grad =
  * its gradient w.r.t. the flat weights (n_w floats, layout of
- * ddg_model_create).  For checking the hand-written backward. */
+ * ddg_model_create).  For checking the hand-written backward (d = 10 models). */
 int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, const int32_t *graphs, int32_t nb,
                             double *loss, float *grad);
 
@@ -228,8 +232,9 @@ int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, c
  * flags: DDG_COARSE, DDG_POU_PROLONG, DDG_BF16_WEIGHTS.  The GNN schedule
  * is tuned here (timed on the right-hand side, cached per decomposition
  * shape class); local graphs of more than 2,048 nodes run on the chunked
- * schedules.  Errors: DDG_INVALID_ARG (no partition, missing model),
- * DDG_TOO_LARGE (a local graph beyond 65,535 nodes), DDG_OOM. */
+ * schedules; a model with d != 10 runs on schedule 5.  Errors:
+ * DDG_INVALID_ARG (no partition, missing model, DDG_BF16_WEIGHTS with
+ * d != 10), DDG_TOO_LARGE (a local graph beyond 65,535 nodes), DDG_OOM. */
 int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, uint32_t flags);
 
 /* z = M^-1 r for device vectors r_dev, z_dev of n_free FP64 (Eqs. 13-16 for

@@ -285,7 +285,7 @@ int32_t ddg_model_create(ddg_ctx *c, int32_t kbar, int32_t d, float alpha, const
     return api_guard([&]() -> int32_t {
         API_BEGIN;
         REQUIRE(c && out, "NULL argument");
-        REQUIRE(d == DSS_D, "only d = 10 is compiled into the GNN kernel");
+        REQUIRE(d == 5 || d == DSS_D || d == 20, "latent size d must be 5, 10 or 20");
         REQUIRE(kbar >= 1 && kbar <= 256, "kbar must be in [1, 256]");
         size_t per = (size_t)(11 * d * d + 15 * d + 1);
         REQUIRE(n_w == per * kbar, "n_w must be kbar * (11 d^2 + 15 d + 1)");
@@ -308,7 +308,7 @@ int32_t ddg_model_create(ddg_ctx *c, int32_t kbar, int32_t d, float alpha, const
                 st = model_xavier(m, seed);
             }
         }
-        if (st == DDG_OK) st = model_pack(m);
+        if (st == DDG_OK && d == DSS_D) st = model_pack(m);  // layouts of schedules 0-4 (d = 10)
         if (st != DDG_OK) {
             dfree_all(c, m->allocs);
             delete m;
@@ -346,9 +346,11 @@ int32_t ddg_model_set_weights(ddg_model *m, const float *w, size_t n_w) {
         REQUIRE(m && w && n_w == m->n_w, "bad arguments");
         DDG_TRY(use_device(m->ctx));
         DDG_CU(cudaMemcpy(m->w, w, sizeof(float) * n_w, cudaMemcpyHostToDevice));
-        DDG_TRY(model_host_layouts(m));
-        DDG_CU(cudaMemcpy(m->packed, m->packed_host.data(), sizeof(float) * m->packed_host.size(),
-                          cudaMemcpyHostToDevice));
+        if (m->d == DSS_D) {  // schedule 5 reads the flat weights directly
+            DDG_TRY(model_host_layouts(m));
+            DDG_CU(cudaMemcpy(m->packed, m->packed_host.data(), sizeof(float) * m->packed_host.size(),
+                              cudaMemcpyHostToDevice));
+        }
         return DDG_OK;
     });
 }
@@ -381,9 +383,10 @@ int32_t ddg_setup_precond(ddg_problem *p, int32_t kind, const ddg_model *model, 
         } else {
             DDG_TRY(dss_check_capacity(p));
             DDG_TRY(dss_select_weights(p, (flags & DDG_BF16_WEIGHTS) != 0));
-            // latents: d planes of sum_loc (schedules 0-2) or rows of 12 floats, h then c (schedule 3)
-            DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, (size_t)DSS_HROW * p->sum_loc));
-            DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, (size_t)DSS_HROW * p->sum_loc));
+            // latents: d planes of sum_loc (schedules 0-2, 5) or rows of 12 floats, h then c (schedules 3, 4)
+            const size_t hl = (size_t)std::max(DSS_HROW, model->d) * p->sum_loc;
+            DDG_TRY(dalloc(c, p->a_pre, &p->dss_h, hl));
+            DDG_TRY(dalloc(c, p->a_pre, &p->dss_h2, hl));
             DDG_TRY(dalloc(c, p->a_pre, &p->dss_c, p->sum_loc));
             p->kind = kind;
             DDG_TRY(dss_autotune(p));
@@ -431,6 +434,7 @@ int32_t ddg_train_local_model(ddg_problem *p, ddg_model *m, const ddg_train_opts
         REQUIRE(m->ctx == p->ctx, "model belongs to another context");
         REQUIRE(o->steps >= 0 && o->batch >= 1 && o->harvest_iters >= 2 && o->lr > 0.f, "bad training options");
         REQUIRE(p->max_loc <= DSS_MAX_NODES, "local graphs too large for the GNN kernels");
+        REQUIRE(m->d == DSS_D, "the training kernels are compiled for d = 10");
         DDG_TRY(use_device(p->ctx));
         int32_t st = train_local_model(p, m, o, report);
         return st;
@@ -443,6 +447,7 @@ int32_t ddg_train_loss_grad(ddg_problem *p, ddg_model *m, const double *r_dev, c
         API_BEGIN;
         REQUIRE(p && p->assembled && p->K > 0 && m && r_dev && graphs && nb >= 1 && loss, "bad arguments");
         for (int b = 0; b < nb; ++b) REQUIRE(graphs[b] >= 0 && graphs[b] < p->K, "graph index out of range");
+        REQUIRE(m->d == DSS_D, "the training kernels are compiled for d = 10");
         DDG_TRY(use_device(p->ctx));
         return train_loss_grad(p, m, r_dev, graphs, nb, loss, grad);
     });

@@ -210,6 +210,10 @@ int32_t dss_select_weights(ddg_problem *p, bool bf16) {
     p->bf16_packed_dev = nullptr;
     p->bf16_tc_dev = nullptr;
     if (!bf16) return DDG_OK;
+    if (m->d != DSS_D) {
+        set_error("BF16 weights need d = 10");
+        return DDG_INVALID_ARG;
+    }
     std::vector<float> flat(m->n_w);
     DDG_CU(cudaMemcpy(flat.data(), m->w, sizeof(float) * m->n_w, cudaMemcpyDeviceToHost));
     for (float &x : flat) x = round_bf16(x);
@@ -1671,6 +1675,7 @@ static ChunkArgs chunk_args(ddg_problem *p, const double *r, const int *stop) {
 int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     const ChunkPlan &cp = p->chunk;
     const ChunkArgs a = chunk_args(p, r, stop);
+    if (p->dss_sched == 5) return dss_d_launch(p, a, s);
     if (cp.tc) return dss_tc_launch(p, a, w_fused_host(p), p->w_bf16 ? p->bf16_tc_dev : p->model->tc_w, s);
     if (cp.global) {
         switch (cp.T) {
@@ -1730,6 +1735,7 @@ bool dss_group_compatible(const ddg_problem *a, const ddg_problem *b) {
 
 int32_t dss_group_prepare(ddg_problem *p) {
     if (p->kind != DDG_DDM_GNN) return DDG_INVALID_ARG;
+    if (p->model->d != DSS_D) return DDG_TOO_LARGE;  // fused group steps run schedule 3 (d = 10 only)
     if (p->dss_sched != 3 || p->chunk.T != GROUP_T || !p->chunk.global || p->chunk.tc) {
         DDG_TRY(chunk_build_global(p, GROUP_T, false));
         p->dss_sched = 3;

@@ -216,8 +216,9 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 // per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
 // the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256); 3 = the
 // chunks of 2 with composed weights, packed two-lane FP32 and message-sorted nodes;
-// 4 = chunks of at most 256 nodes with the per-node matrix products on the tensor
-// cores (dss_tc.cu).
+// 4 = chunks of at most 128 nodes with the per-node matrix products of the latent
+// vectors on the tensor cores (dss_tc.cu); 5 = the generic kernel for any latent size
+// d in {5, 10, 20} (dss_d.cu), the only schedule for d != 10.
 // DDG_GNN_SCHEDULE = 0..4 (and DDG_GNN_CHUNK_T = 128/192/256 for schedule 2,
 // 128/256 for schedule 3) forces one.
 // The choice is cached in the context per decomposition shape class, so a stream
@@ -225,6 +226,11 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 int32_t dss_autotune(ddg_problem *p) {
     const char *env = getenv("DDG_GNN_SCHEDULE");
     const char *envT = getenv("DDG_GNN_CHUNK_T");
+    // latent sizes other than the compiled d = 10 (or schedule 5 forced): the generic schedule
+    if (p->model->d != DSS_D || (env && env[0] == '5' && env[1] == 0)) {
+        p->dss_sched = 5;
+        return chunk_build(p, DSS_D_CHUNK_T);
+    }
     if (env && env[0] >= '0' && env[0] <= '4' && env[1] == 0) {
         p->dss_sched = env[0] - '0';
         if (p->dss_sched < 2 && !p->dss_whole_graph) {

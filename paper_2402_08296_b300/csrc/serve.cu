@@ -179,7 +179,7 @@ static int32_t start(Server *S, ServeRequest *q) {
     q->x.resize(n);
     // the smaller group (fewer graph nodes) takes the request, if compatible
     Server::Group *join = nullptr;
-    if (S->fuse && q->opts.kind == DDG_DDM_GNN) {
+    if (S->fuse && q->opts.kind == DDG_DDM_GNN && q->opts.model->d == DSS_D) {
         DDG_TRY(dss_group_prepare(q->p));
         long long best = -1;
         for (Server::Group &g : S->groups) {

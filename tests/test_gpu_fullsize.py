@@ -96,7 +96,7 @@ def test_full_coarse_matrix_and_inverse(ddg, torch, full):
     A0, A0inv = ddg.ddg_coarse_download(p)
     K = A0.shape[0]
     assert np.max(np.abs(A0 - D.A0)) <= 1e-12 * np.abs(D.A0).max()
-    assert np.array_equal(A0, A0.T)
+    assert np.max(np.abs(A0 - A0.T)) <= 1e-13 * np.abs(A0).max()   # symmetric up to summation order
     assert np.max(np.abs(A0inv @ D.A0 - np.eye(K))) < 1e-8
     import scipy.linalg as sla
     r = synth.residual_vector(P.n_free, 80)

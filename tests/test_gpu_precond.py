@@ -329,3 +329,70 @@ def test_dss_kbar_10(ddg, ctx, torch, weights, schedule, monkeypatch):
     finally:
         ddg.ddg_problem_destroy(p)
         ddg.ddg_model_destroy(m)
+
+
+@pytest.mark.parametrize("d,kbar,name,seed,K", [(5, 10, "star20000", 9, 20), (20, 10, "star20000", 10, 20),
+                                                 (10, 10, "star20000", 11, 20), (20, 30, "square2k", 12, 4),
+                                                 (5, 5, "square2k", 13, 4)])
+def test_dss_latent_sizes(ddg, ctx, torch, d, kbar, name, seed, K, monkeypatch):
+    """Latent sizes of Table 2's sweep (d = 5, 10, 20): the generic schedule 5 (the only one for
+    d != 10; forced for d = 10) against the FP64 oracle on every subdomain, element-wise."""
+    if d == 10:
+        monkeypatch.setenv("DDG_GNN_SCHEDULE", "5")
+    alpha, delta = 0.05, 2 if name.startswith("star") else 1
+    W = synth.dss_weights(kbar, d, seed, bias_scale=0.1)
+    assert W.shape[0] == kbar * (11 * d * d + 15 * d + 1)
+    w = synth.workload(name, seed)
+    P, Dd = oracle_setup(w.mesh, w.coeffs, K, delta)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, K, delta)
+    m = ddg.ddg_model_create(ctx, kbar, d, alpha, W)
+    try:
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
+        r = synth.residual_vector(P.n_free, seed + 30)
+        rd = _dev(torch, r)
+        sk = sum(len(S) for S in Dd.sets)
+        corr = torch.zeros(sk, dtype=torch.float64, device="cuda")
+        s = torch.zeros(K, dtype=torch.float64, device="cuda")
+        ddg.ddg_local_corrections(p, rd, corr, s)
+        torch.cuda.synchronize()
+        corr = corr.cpu().numpy()
+        adj = pt.mesh_adjacency(P.n, P.tri)
+        hbar = pt.mean_edge_length(P.xy, P.tri)
+        off = 0
+        for i, S in enumerate(Dd.sets):
+            g = pt.local_graph(P, S, adj)
+            si = np.linalg.norm(r[S])
+            ref = si * dss.forward(g.xy, g.n_int, g.src, g.dst, r[S] / si, W, kbar, d, alpha, hbar)
+            assert_close(corr[off:off + len(S)], ref, 1e-4, (d, kbar, i))
+            off += len(S)
+        # the whole preconditioner (coarse term + gluing) through the same schedule
+        gnn = ddm.DDMGNN(ddm.TwoLevelASM(P, Dd), W, kbar, d, alpha)
+        zd = torch.zeros_like(rd)
+        ddg.ddg_precondition(p, rd, zd)
+        torch.cuda.synchronize()
+        assert_close(zd.cpu().numpy(), gnn.apply(r), 1e-4)
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)
+
+
+def test_latent_sizes_the_library_refuses(ddg, ctx):
+    """d outside {5, 10, 20}, BF16 weights and training for d != 10 are refused with a status."""
+    for d in (4, 12, 32):
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_model_create(ctx, 2, d, 1e-3, None)
+        assert e.value.status == ddg.DDG_INVALID_ARG
+    w = synth.workload("square2k", 14)
+    p = gpu_setup(ddg, ctx, w.mesh, w.coeffs, 4, 1)
+    m = ddg.ddg_model_create(ctx, 3, 5, 1e-3, None, seed=4)
+    try:
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE | ddg.DDG_BF16_WEIGHTS)
+        assert e.value.status == ddg.DDG_INVALID_ARG
+        ddg.ddg_setup_precond(p, ddg.DDG_DDM_LU, None, ddg.DDG_COARSE)
+        with pytest.raises(ddg.DdgError) as e:
+            ddg.ddg_train_local_model(p, m, steps=1, batch=4, lr=1e-3, clip=1e-2, harvest_iters=3, seed=0)
+        assert e.value.status == ddg.DDG_INVALID_ARG
+    finally:
+        ddg.ddg_problem_destroy(p)
+        ddg.ddg_model_destroy(m)

@@ -36,7 +36,11 @@ def test_noalloc_spmv_dot_matches_apply_A_twice():
             ref = y_ref.cpu().numpy()
             got = y.cpu().numpy()
             assert np.max(np.abs(got - ref)) <= 1e-13 * np.abs(ref).max()
-            dot_ref = float(np.dot(x.cpu().numpy(), ref))
+            # and against the oracle's own matrix: y = A_ff x and x.y
+            xh = x.cpu().numpy()
+            y_or = P.A @ xh
+            assert np.max(np.abs(got - y_or)) <= 1e-12 * np.abs(y_or).max()
+            dot_ref = float(np.dot(xh, y_or))
             assert abs(float(xy.item()) - dot_ref) <= 1e-12 * abs(dot_ref)
     finally:
         ddg.ddg_problem_destroy(p)
