@@ -206,6 +206,9 @@ struct ddg_problem {
     int *lu_bw = nullptr;       // [K]
     long long *lu_off = nullptr; // [K+1] start of each band factor
     double *lu_band = nullptr;
+    double *lu_bandT = nullptr;      // the factor's transpose, same storage (backward solves)
+    long long *lu_toff = nullptr;    // [K+1] start of each subdomain's diagonal-tile inverses
+    double *lu_tinv = nullptr;       // 32 x 32 inverse of every diagonal tile of L, row-major
     int lu_kmax = 0;
     double *s = nullptr, *y = nullptr, *wc = nullptr, *corr = nullptr;
     // GNN weights in use: the model's, or (DDG_BF16_WEIGHTS) this problem's copies rounded to bfloat16
@@ -216,7 +219,8 @@ struct ddg_problem {
     bool dss_whole_graph = true;  // every local graph fits one CTA (schedules 0 and 1 allowed)
     int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block,
                                 // 3 chunked per block with composed weights and packed two-lane FP32,
-                                // 4 as 3 with the per-node matrix products on the tensor cores
+                                // 4 as 3 with the per-node matrix products on the tensor cores,
+                                // 5 any latent size d in {5, 10, 20} (flat weights, schedule 2's chunks)
     float *dss_h = nullptr, *dss_c = nullptr;  // latents and c between launches (schedules 1, 2)
     float *dss_h2 = nullptr;    // second latent buffer (schedule 2)
     ChunkPlan chunk;
@@ -307,13 +311,16 @@ int32_t chunk_build(ddg_problem *p, int T);
 struct ChunkArgs;
 int32_t chunk_build_global(ddg_problem *p, int T, bool tc);
 // schedule 4 (dss_tc.cu): per-node matrix products of the GNN on the tensor cores
-constexpr int TC_T = 256;            // threads of a CTA, and own nodes of a chunk at most
-constexpr int TC_NEED = 384;         // needed nodes of a chunk at most (three 128-row tiles)
-constexpr int TCW_FLOATS = 3328;     // floats of one block's tensor-core weight image
-constexpr size_t TC_SMEM = 96512;    // dynamic shared memory of a schedule-4 CTA (at most two per SM)
+constexpr int TC_T = 128;            // threads of a CTA, and own nodes of a chunk at most
+constexpr int TC_NEED = 256;         // needed nodes of a chunk at most (two 128-row tiles)
+constexpr int TCW_FLOATS = 2048;     // floats of one block's tensor-core weight image
+constexpr size_t TC_SMEM = 49152;    // dynamic shared memory of a schedule-4 CTA (at most four per SM)
 void tc_weight_image(const float *fused, int kbar, std::vector<float> &img);
 int32_t tc_ctas_per_sm(int *out);
 int32_t dss_tc_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *tc_w, cudaStream_t s);
+// schedule 5 (dss_d.cu): latent sizes d = 5, 10, 20 from the flat weights, on schedule 2's chunks
+constexpr int DSS_D_CHUNK_T = 128;
+int32_t dss_d_launch(ddg_problem *p, const ChunkArgs &a, cudaStream_t s);
 // fused GNN steps over several problems (request loop): schedule 3 with chunk width GROUP_T
 constexpr int GROUP_T = 128;
 int32_t dss_group_prepare(ddg_problem *p);

@@ -179,90 +179,134 @@ __global__ void __launch_bounds__(LU_T) k_lu_factor(const int *sub_ptr, const in
     if (threadIdx.x == 0 && bad) raise_status(st, ST_BAD_INPUT);
 }
 
-// forward and backward band solves, one CTA per subdomain, rows in tiles of 32:
-// the CTA stages each 32 x 32 diagonal tile of the factor in shared memory with
-// coalesced loads, a warp solves it from there, and the whole CTA applies the
-// band entries outside it; corr is written in sub_idx order
+// The solves run in tiles of 32 rows.  Set-up keeps, besides the factor, its transpose in
+// the same band storage (row c holds L[c .. c + bw][c], diagonal first) so that the backward
+// solve reads rows contiguously too, and the inverse of every 32 x 32 diagonal tile of L
+// (lower triangular), so that a tile's triangular solve is one small matrix-vector product
+// instead of 32 dependent steps.
 constexpr int LU_TILE = 32;
+static_assert(LU_T == LU_TILE * 8, "a solve CTA is 32 rows of 8 threads");
 
-// Ds[rr][cc] = L[r0 + rr][r0 + cc] inside the band (diagonal slot: 1 / L_rr), 0 elsewhere
-__device__ __forceinline__ void lu_stage_tile(double (*Ds)[LU_TILE + 1], const double *B, int w, int bw, int r0,
-                                              int nrow) {
-    for (int q = threadIdx.x; q < LU_TILE * LU_TILE; q += LU_T) {
-        const int rr = q / LU_TILE, cc = q % LU_TILE;
-        double v = 0.0;
-        if (rr < nrow && cc <= rr && rr - cc <= bw) v = B[(long long)(r0 + rr) * w + (cc - rr + bw)];
-        Ds[rr][cc] = v;
+__global__ void __launch_bounds__(LU_T) k_lu_transpose(const int *sub_ptr, const int *bw_arr, const long long *off,
+                                                       const double *band, double *bandT) {
+    const int i = blockIdx.x;
+    const int k = sub_ptr[i + 1] - sub_ptr[i];
+    const int bw = bw_arr[i], w = bw + 1;
+    const double *B = band + off[i];
+    double *U = bandT + off[i];
+    for (long long qq = threadIdx.x; qq < (long long)k * w; qq += LU_T) {
+        const int c = (int)(qq / w), j = (int)(qq % w);  // U[c][c + j] = L[c + j][c]
+        const int q = c + j;
+        U[qq] = q < k ? B[(long long)q * w + (c - q + bw)] : 0.0;
     }
 }
 
+// inverse of every diagonal tile, one warp per subdomain: lane j computes column j by forward
+// substitution, x_r = (delta_rj - sum_{m<r} L[r][m] x_m) / L[r][r]; rows and columns past the
+// subdomain's end are zero
+__global__ void __launch_bounds__(32) k_lu_tinv(const int *sub_ptr, const int *bw_arr, const long long *off,
+                                               const long long *toff, const double *band, double *tinv) {
+    __shared__ double X[LU_TILE][LU_TILE + 1];
+    const int i = blockIdx.x, lane = threadIdx.x;
+    const int k = sub_ptr[i + 1] - sub_ptr[i];
+    const int bw = bw_arr[i], w = bw + 1;
+    const double *B = band + off[i];
+    double *T = tinv + toff[i];
+    const int nt = (k + LU_TILE - 1) / LU_TILE;
+    for (int t = 0; t < nt; ++t) {
+        const int r0 = t * LU_TILE, nrow = min(LU_TILE, k - r0);
+        for (int r = 0; r < LU_TILE; ++r) {
+            double acc = 0.0;
+            if (r < nrow && lane < nrow && lane <= r) {
+                acc = r == lane ? 1.0 : 0.0;
+                const double *Lr = B + (long long)(r0 + r) * w;
+                for (int m = max(lane, r - bw); m < r; ++m) acc -= Lr[m - r + bw] * X[m][lane];
+                acc *= Lr[bw];  // the diagonal slot holds 1 / L[r][r]
+            }
+            X[r][lane] = acc;
+        }
+        for (int r = 0; r < LU_TILE; ++r) T[(long long)t * LU_TILE * LU_TILE + r * LU_TILE + lane] = X[r][lane];
+        __syncwarp();
+    }
+}
+
+// forward and backward band solves, one CTA per subdomain, 8 threads per row of a tile: the
+// band entries left of (forward) or below (backward) the tile are summed in parallel, then
+// the tile's inverse (or its transpose) is applied; corr is written in sub_idx order
 __global__ void __launch_bounds__(LU_T) k_lu_apply(const int *sub_ptr, const int *sub_idx, const int *lu_pos,
-                                                   const int *bw_arr, const long long *off, const double *band,
+                                                   const int *bw_arr, const long long *off, const long long *toff,
+                                                   const double *band, const double *bandT, const double *tinv,
                                                    const double *r, const double *s, double *corr, const int *stop) {
     extern __shared__ double yv[];
-    __shared__ double Ds[LU_TILE][LU_TILE + 1];
+    __shared__ double rhs[LU_TILE];
     if (stop && *stop) return;
     const int i = blockIdx.x;
     const int s0 = sub_ptr[i], k = sub_ptr[i + 1] - s0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, rr = tid >> 3, part = tid & 7;
     const int bw = bw_arr[i], w = bw + 1;
-    const double *B = band + off[i];
+    const double *B = band + off[i], *U = bandT + off[i], *T = tinv + toff[i];
     if (s[i] == 0.0) {
         for (int t = tid; t < k; t += LU_T) corr[s0 + t] = 0.0;
         return;
     }
     for (int t = tid; t < k; t += LU_T) yv[lu_pos[s0 + t]] = r[sub_idx[s0 + t]];
     __syncthreads();
+    const int nt = (k + LU_TILE - 1) / LU_TILE;
     // L y = b
-    for (int r0 = 0; r0 < k; r0 += LU_TILE) {
-        const int nrow = min(LU_TILE, k - r0);
-        for (int rr = warp; rr < nrow; rr += LU_T / 32) {
-            const int row = r0 + rr;
+    for (int t = 0; t < nt; ++t) {
+        const int r0 = t * LU_TILE, nrow = min(LU_TILE, k - r0), row = r0 + rr;
+        const double *Tt = T + (long long)t * LU_TILE * LU_TILE;
+        double tv[4];  // L_tt^-1 [rr][part + 8 j]: independent of the sums, loaded first
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tv[j] = rr < nrow ? Tt[rr * LU_TILE + part + 8 * j] : 0.0;
+        double acc = 0.0;
+        if (rr < nrow) {
             const double *Lr = B + (long long)row * w;
-            double acc = 0.0;
-            for (int c = max(0, row - bw) + lane; c < r0; c += 32) acc += Lr[c - row + bw] * yv[c];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) yv[row] -= acc;
+#pragma unroll 4
+            for (int c = max(0, row - bw) + part; c < r0; c += 8) acc += Lr[c - row + bw] * yv[c];
         }
-        lu_stage_tile(Ds, B, w, bw, r0, nrow);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (part == 0 && rr < nrow) rhs[rr] = yv[row] - acc;
         __syncthreads();
-        if (warp == 0) {
-            const int row = r0 + lane;
-            double y = lane < nrow ? yv[row] : 0.0;
-            for (int j = 0; j < nrow; ++j) {
-                if (lane == j) y *= Ds[j][j];
-                const double xj = __shfl_sync(0xffffffffu, y, j);
-                if (lane > j && lane < nrow && lane - j <= bw) y -= Ds[lane][j] * xj;
-            }
-            if (lane < nrow) yv[row] = y;
-        }
+        double y = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (part + 8 * j < nrow) y += tv[j] * rhs[part + 8 * j];
+        y += __shfl_xor_sync(0xffffffffu, y, 4);
+        y += __shfl_xor_sync(0xffffffffu, y, 2);
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        if (part == 0 && rr < nrow) yv[row] = y;
         __syncthreads();
     }
     // L^T x = y, tiles from the bottom
-    for (int r0 = ((k - 1) / LU_TILE) * LU_TILE; r0 >= 0; r0 -= LU_TILE) {
-        const int nrow = min(LU_TILE, k - r0);
-        lu_stage_tile(Ds, B, w, bw, r0, nrow);
-        __syncthreads();
-        if (warp == 0) {
-            const int row = r0 + lane;
-            double y = lane < nrow ? yv[row] : 0.0;
-            const double dinv = lane < nrow ? Ds[lane][lane] : 0.0;
-            for (int j = nrow - 1; j >= 0; --j) {
-                if (lane == j) y *= dinv;
-                const double xj = __shfl_sync(0xffffffffu, y, j);
-                if (lane < j && j - lane <= bw) y -= Ds[j][lane] * xj;
-            }
-            if (lane < nrow) yv[row] = y;
+    for (int t = nt - 1; t >= 0; --t) {
+        const int r0 = t * LU_TILE, nrow = min(LU_TILE, k - r0), row = r0 + rr, r1 = r0 + nrow - 1;
+        const double *Tt = T + (long long)t * LU_TILE * LU_TILE;
+        double tv[4];  // (L_tt^-1)^T [rr][part + 8 j]
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tv[j] = rr < nrow ? Tt[(part + 8 * j) * LU_TILE + rr] : 0.0;
+        double acc = 0.0;
+        if (rr < nrow) {
+            const double *Ur = U + (long long)row * w;  // Ur[j] = L[row + j][row]
+            const int qmax = min(k - 1, row + bw);
+#pragma unroll 4
+            for (int q = r1 + 1 + part; q <= qmax; q += 8) acc += Ur[q - row] * yv[q];
         }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (part == 0 && rr < nrow) rhs[rr] = yv[row] - acc;
         __syncthreads();
-        for (int c = max(0, r0 - bw) + tid; c < r0; c += LU_T) {
-            double acc = 0.0;
-            for (int qq = 0; qq < nrow; ++qq) {
-                const int q = r0 + qq;
-                if (q - c <= bw) acc += B[(long long)q * w + (c - q + bw)] * yv[q];
-            }
-            yv[c] -= acc;
-        }
+        double x = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (part + 8 * j < nrow) x += tv[j] * rhs[part + 8 * j];
+        x += __shfl_xor_sync(0xffffffffu, x, 4);
+        x += __shfl_xor_sync(0xffffffffu, x, 2);
+        x += __shfl_xor_sync(0xffffffffu, x, 1);
+        if (part == 0 && rr < nrow) yv[row] = x;
         __syncthreads();
     }
     for (int t = tid; t < k; t += LU_T) corr[s0 + t] = yv[lu_pos[s0 + t]];
@@ -307,6 +351,17 @@ int32_t lu_build(ddg_problem *p) {
     DDG_LAUNCH_CHECK();
     k_lu_factor<<<K, LU_T, 0, s>>>(p->sub_ptr, p->lu_bw, p->lu_off, p->lu_band, p->d_status);
     DDG_LAUNCH_CHECK();
+    // the transposed band and the diagonal tiles' inverses of the solves
+    std::vector<long long> toff(K + 1, 0);
+    for (int i = 0; i < K; ++i) toff[i + 1] = toff[i] + (long long)((hp[i + 1] - hp[i] + LU_TILE - 1) / LU_TILE) * LU_TILE * LU_TILE;
+    DDG_TRY(dalloc(c, p->a_pre, &p->lu_toff, K + 1));
+    DDG_CU(cudaMemcpyAsync(p->lu_toff, toff.data(), sizeof(long long) * (K + 1), cudaMemcpyHostToDevice, s));
+    DDG_TRY(dalloc(c, p->a_pre, &p->lu_bandT, off[K]));
+    DDG_TRY(dalloc(c, p->a_pre, &p->lu_tinv, toff[K]));
+    k_lu_transpose<<<K, LU_T, 0, s>>>(p->sub_ptr, p->lu_bw, p->lu_off, p->lu_band, p->lu_bandT);
+    DDG_LAUNCH_CHECK();
+    k_lu_tinv<<<K, 32, 0, s>>>(p->sub_ptr, p->lu_bw, p->lu_off, p->lu_toff, p->lu_band, p->lu_tinv);
+    DDG_LAUNCH_CHECK();
     DDG_CU(cudaStreamSynchronize(s));
     p->lu_kmax = kmax;
     int32_t r = check_status(p, "band Cholesky");
@@ -316,7 +371,8 @@ int32_t lu_build(ddg_problem *p) {
 
 int32_t lu_apply_launch(ddg_problem *p, const double *r, const int *stop, cudaStream_t s) {
     k_lu_apply<<<p->K, LU_T, sizeof(double) * p->lu_kmax, s>>>(p->sub_ptr, p->sub_idx, p->lu_pos, p->lu_bw,
-                                                             p->lu_off, p->lu_band, r, p->s, p->corr, stop);
+                                                             p->lu_off, p->lu_toff, p->lu_band, p->lu_bandT,
+                                                             p->lu_tinv, r, p->s, p->corr, stop);
     DDG_LAUNCH_CHECK();
     return DDG_OK;
 }
