@@ -143,6 +143,8 @@ struct ChunkPlan {
     int *c_graph = nullptr, *c_n0 = nullptr, *c_own = nullptr, *c_need_off = nullptr, *c_need_n = nullptr;
     int *need = nullptr, *c_adj_off = nullptr, *adj_ptr = nullptr, *c_adj_base = nullptr;
     uint16_t *adj = nullptr;
+    uint2 *adjx = nullptr;  // schedule 4: per adjacency entry {chunk-local neighbour, edge length |d| as float
+                            //   bits}, each own node's unknown neighbours first
     ddg::Allocs allocs;
 };
 
@@ -313,8 +315,9 @@ int32_t chunk_build_global(ddg_problem *p, int T, bool tc);
 // schedule 4 (dss_tc.cu): per-node matrix products of the GNN on the tensor cores
 constexpr int TC_T = 128;            // threads of a CTA, and own nodes of a chunk at most
 constexpr int TC_NEED = 256;         // needed nodes of a chunk at most (two 128-row tiles)
-constexpr int TCW_FLOATS = 2048;     // floats of one block's tensor-core weight image
-constexpr size_t TC_SMEM = 49152;    // dynamic shared memory of a schedule-4 CTA (at most four per SM)
+constexpr int TCW_FLOATS = 3328;     // floats of one block's tensor-core weight images (three GEMMs)
+constexpr size_t TC_SMEM = 47104;    // dynamic shared memory of a schedule-4 CTA (at most four per SM)
+constexpr int TC_CTAS_PER_SM = 4;    // schedule-4 CTAs an SM holds (4 x 128 tensor-memory columns)
 void tc_weight_image(const float *fused, int kbar, std::vector<float> &img);
 int32_t tc_ctas_per_sm(int *out);
 int32_t dss_tc_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *tc_w, cudaStream_t s);

@@ -1071,7 +1071,7 @@ __global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int
                                                       const int *sub_idx, int pass, int *need_n, int *adj_n,
                                                       const int *need_off, int *need, const int *adj_off,
                                                       int *adj_ptr, const int *adj_base, uint16_t *adj, int4 *info,
-                                                      int *st) {
+                                                      const float2 *loc_xy, uint2 *adjx, int *st) {
     constexpr int NT = 256, MAXN = 2048, MAXO = 512;
     __shared__ int cand[MAXN];
     __shared__ int work[MAXO], slot[MAXO], order[MAXO], sptr[MAXO + 1];
@@ -1199,26 +1199,38 @@ __global__ void __launch_bounds__(256) k_gchunk_build(const int *c_n0, const int
     }
     for (int t = threadIdx.x; t < ext; t += NT) nd[own + t] = cand[t];
     for (int r = threadIdx.x; r <= own; r += NT) ap[r] = sptr[r];
+    // schedule 4 (adjx given): each node's unknown neighbours first, with the edge length
     for (int r = threadIdx.x; r < own; r += NT) {
         int g, lp, e0, e1;
         row(order[r], g, lp, e0, e1);
         const uint16_t *gn = nbr + nbr_off[g];
         const int k = loc_nint[g];
+        const float2 xj = loc_xy[o0 + order[r]];
         int pos = sptr[r];
-        for (int e = e0; e < e1; ++e, ++pos) {
-            const int l = lp + gn[e];
-            int v;
-            if (l >= o0 && l < o0 + own) {
-                v = slot[l - o0];
-            } else {
-                int lo = 0, hi = ext;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cand[mid] < l) lo = mid + 1; else hi = mid;
+        for (int pass2 = 0; pass2 < (adjx ? 2 : 1); ++pass2) {
+            for (int e = e0; e < e1; ++e) {
+                const bool unknown = gn[e] < k;
+                if (adjx && unknown != (pass2 == 0)) continue;
+                const int l = lp + gn[e];
+                int v;
+                if (l >= o0 && l < o0 + own) {
+                    v = slot[l - o0];
+                } else {
+                    int lo = 0, hi = ext;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (cand[mid] < l) lo = mid + 1; else hi = mid;
+                    }
+                    v = own + lo;
                 }
-                v = own + lo;
+                ad[pos] = (uint16_t)(v | (unknown ? 0x8000 : 0));
+                if (adjx) {
+                    const float2 xl = loc_xy[l];
+                    const float dx = xl.x - xj.x, dy = xl.y - xj.y;
+                    adjx[adj_base[q] + pos] = make_uint2((unsigned)v, __float_as_uint(sqrtf(fmaf(dx, dx, dy * dy))));
+                }
+                ++pos;
             }
-            ad[pos] = (uint16_t)(v | (gn[e] < k ? 0x8000 : 0));
         }
     }
 }
@@ -1325,6 +1337,7 @@ void chunk_free(ddg_problem *p) {
     p->chunk.c_graph = p->chunk.c_n0 = p->chunk.c_own = p->chunk.c_need_off = p->chunk.c_need_n = nullptr;
     p->chunk.need = p->chunk.c_adj_off = p->chunk.adj_ptr = p->chunk.c_adj_base = nullptr;
     p->chunk.adj = nullptr;
+    p->chunk.adjx = nullptr;
     p->chunk.gid = nullptr;
     p->chunk.info = nullptr;
     p->chunk.global = false;
@@ -1466,6 +1479,7 @@ int32_t chunk_build_global(ddg_problem *p, int T, bool tc) {
             return DDG_INVALID_ARG;
         }
         DDG_TRY(tc_ctas_per_sm(&per_sm));
+        per_sm = TC_CTAS_PER_SM;  // the launch's grid (dss_tc_launch)
     } else {
         const size_t smem_est = fused_smem(3 * T, 2 * T);  // 2T own + T outside nodes
         switch (T) {
@@ -1527,7 +1541,8 @@ int32_t chunk_build_global(ddg_problem *p, int T, bool tc) {
         DDG_CU(cudaMemcpyAsync(t_own, cown.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
         k_gchunk_build<<<nc, 256, 0, s>>>(t_n0, t_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
                                           p->nbr, p->sub_ptr, p->sub_idx, 0, t_need, t_adj, nullptr, nullptr,
-                                          nullptr, nullptr, nullptr, nullptr, nullptr, p->d_status);
+                                          nullptr, nullptr, nullptr, nullptr, nullptr, p->loc_xy, nullptr,
+                                          p->d_status);
         DDG_LAUNCH_CHECK();
         hn.assign(nc, 0);
         ha.assign(nc, 0);
@@ -1597,13 +1612,15 @@ int32_t chunk_build_global(ddg_problem *p, int T, bool tc) {
     }
     DDG_TRY(dalloc(c, cp.allocs, &cp.need, tn));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj, ta));
+    if (tc) DDG_TRY(dalloc(c, cp.allocs, &cp.adjx, ta));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj_ptr, tp));
     DDG_CU(cudaMemcpyAsync(cp.c_need_off, noff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_adj_off, aoff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_adj_base, abase.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
                                       p->nbr, p->sub_ptr, p->sub_idx, 1, nullptr, nullptr, cp.c_need_off, cp.need,
-                                      cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->d_status);
+                                      cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->loc_xy,
+                                      tc ? cp.adjx : nullptr, p->d_status);
     DDG_LAUNCH_CHECK();
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
@@ -1651,6 +1668,7 @@ static ChunkArgs chunk_args(ddg_problem *p, const double *r, const int *stop) {
     a.c_adj_off = cp.c_adj_off;
     a.adj_ptr = cp.adj_ptr;
     a.adj = cp.adj;
+    a.adjx = cp.adjx;
     a.c_adj_base = cp.c_adj_base;
     a.loc_ptr = p->loc_ptr;
     a.loc_nint = p->loc_nint;

@@ -209,6 +209,7 @@ struct ChunkArgs {
     const int *c_adj_off;                   // per chunk: start of its own nodes' CSR in adj_ptr
     const int *adj_ptr;                     // own-node CSR offsets (relative to the chunk's adj start)
     const uint16_t *adj;                    // chunk-local neighbour ids
+    const uint2 *adjx;                      // schedule 4: {chunk-local neighbour id, |d| float bits}, unknowns first
     const int *c_adj_base;                  // per chunk: start of its slice in adj
     const int *loc_ptr, *loc_nint, *sub_ptr, *sub_idx;
     const int *gid;                         // global plans: graph of every local node
