@@ -40,7 +40,7 @@ METRIC = "Poisson solves/s to rel.res 1e-6, GNN vs LU-Schwarz on 1 B300; p50/p99
 KBAR, D, ALPHA = 30, 10, 1e-3
 WEIGHTS = os.path.join(ROOT, "paper_2402_08296_b300", "weights", "dss_k30_d10.npy")
 L2_FLUSH_BYTES = 512 << 20
-GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused", 4: "k_dss_tc"}
+GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused", 4: "k_dss_tc", 5: "k_dss_d", 6: "k_dss_mma"}
 # DRAM bytes (read + write) per GNN application from an ncu capture of the current kernel form,
 # keyed by (workload, schedule, chunk width); absent (null in the line) when no capture of the
 # current kernel exists for the workload.  Filled from the committed profiles.

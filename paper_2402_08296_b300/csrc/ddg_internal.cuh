@@ -125,6 +125,7 @@ struct ddg_model {
     std::vector<float> packed_host;  // the same packed weights on the host (kernel-parameter copies)
     std::vector<float> fused_host;   // composed per-block layout of the fused GNN kernel (kernel parameters)
     float *tc_w = nullptr;           // per-block tensor-core weight images of schedule 4 (device)
+    float *mma_w = nullptr;          // per-block warp-MMA weight fragments of schedule 6 (device)
     float *adam_m = nullptr, *adam_v = nullptr;  // Adam moments, kept across training calls
     long long adam_t = 0;
     ddg::Allocs allocs;
@@ -217,6 +218,7 @@ struct ddg_problem {
     bool w_bf16 = false;
     float *bf16_packed_dev = nullptr;
     float *bf16_tc_dev = nullptr;   // schedule-4 weight images of the rounded weights
+    float *bf16_mma_dev = nullptr;  // schedule-6 weight fragments of the rounded weights
     std::vector<float> bf16_packed_host, bf16_fused_host;
     bool dss_whole_graph = true;  // every local graph fits one CTA (schedules 0 and 1 allowed)
     int dss_sched = 0;          // GNN schedule: 0 one persistent launch, 1 one launch per block, 2 chunked per block,
@@ -321,6 +323,12 @@ constexpr int TC_CTAS_PER_SM = 4;    // schedule-4 CTAs an SM holds (4 x 128 ten
 void tc_weight_image(const float *fused, int kbar, std::vector<float> &img);
 int32_t tc_ctas_per_sm(int *out);
 int32_t dss_tc_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *tc_w, cudaStream_t s);
+// schedule 6 (dss_mma.cu): schedule 4's chunks, per-node products as warp-synchronous tensor-core MMAs
+constexpr int MMA_W_FLOATS = 3072;  // floats of one block's MMA weight fragments (four products)
+void mma_weight_image(const float *fused, int kbar, std::vector<float> &img);
+int32_t mma_ctas_per_sm(int *out);
+int32_t dss_mma_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *mma_w,
+                       cudaStream_t s);
 // schedule 5 (dss_d.cu): latent sizes d = 5, 10, 20 from the flat weights, on schedule 2's chunks
 constexpr int DSS_D_CHUNK_T = 128;
 int32_t dss_d_launch(ddg_problem *p, const ChunkArgs &a, cudaStream_t s);

@@ -172,6 +172,9 @@ int32_t model_host_layouts(ddg_model *m) {
     tc_weight_image(m->fused_host.data(), m->kbar, img);
     if (!m->tc_w) DDG_TRY(dalloc(m->ctx, m->allocs, &m->tc_w, img.size()));
     DDG_CU(cudaMemcpy(m->tc_w, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
+    mma_weight_image(m->fused_host.data(), m->kbar, img);
+    if (!m->mma_w) DDG_TRY(dalloc(m->ctx, m->allocs, &m->mma_w, img.size()));
+    DDG_CU(cudaMemcpy(m->mma_w, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
     return DDG_OK;
 }
 
@@ -209,6 +212,7 @@ int32_t dss_select_weights(ddg_problem *p, bool bf16) {
     p->w_bf16 = bf16;
     p->bf16_packed_dev = nullptr;
     p->bf16_tc_dev = nullptr;
+    p->bf16_mma_dev = nullptr;
     if (!bf16) return DDG_OK;
     if (m->d != DSS_D) {
         set_error("BF16 weights need d = 10");
@@ -229,6 +233,11 @@ int32_t dss_select_weights(ddg_problem *p, bool bf16) {
     DDG_TRY(dalloc(p->ctx, p->a_pre, &tdev, img.size()));
     DDG_CU(cudaMemcpy(tdev, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
     p->bf16_tc_dev = tdev;
+    mma_weight_image(p->bf16_fused_host.data(), m->kbar, img);
+    float *mdev = nullptr;
+    DDG_TRY(dalloc(p->ctx, p->a_pre, &mdev, img.size()));
+    DDG_CU(cudaMemcpy(mdev, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice));
+    p->bf16_mma_dev = mdev;
     return DDG_OK;
 }
 
@@ -850,7 +859,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     const int nn = a.c_need_n[q];
     const int *need = a.need + a.c_need_off[q];  // local-node ids over all graphs: own nodes first
     const int *APTR = a.adj_ptr + a.c_adj_off[q];      // [own + 1]
-    const uint16_t *ADJ = a.adj + a.c_adj_base[q];     // chunk-local ids, bit 15: neighbour is an unknown
+    const uint2 *ADJX = a.adjx + a.c_adj_base[q];      // {chunk-local id, |d|}, each node's unknowns first
     const int4 *INFO = a.info + a.c_n0[q];             // [own] {node, corr idx, r idx, graph | dout << 24}
     float4 *Pb = smem4;                                               // [nn][5]
     float4 *HS = Pb + (size_t)nn * 5;                                 // [own][3] latent rows of own nodes
@@ -916,7 +925,8 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
         const float2 xj = XY[u];
         const int e0 = APTR[u], e1 = APTR[u + 1];
         f2_t so[D / 2], si[D / 2], pao[D / 2], pai[D / 2];
-        const float dout = (float)((unsigned)inf.w >> 24);  // out-messages (neighbours that are unknowns)
+        const int n_out = min((int)((unsigned)inf.w >> 24), e1 - e0);  // out-messages (neighbours that are unknowns)
+        const float dout = (float)n_out;
 #pragma unroll
         for (int m = 0; m < D / 2; ++m) {
             so[m] = 0ull;
@@ -934,26 +944,50 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
                 pai[m] = f2_fma(Wp[(F_NXA + 3 * D) / 2 + m], y2, f2_fma(Wp[(F_NXA + D) / 2 + m], x2, pai[m]));
             }
         }
-        // the next neighbour's entry is loaded one iteration ahead (its global load overlaps this edge)
-        unsigned ent_next = e0 < e1 ? ADJ[e0] : 0u;
-        for (int e = e0; e < e1; ++e) {
-            const unsigned ent = ent_next;
-            if (e + 1 < e1) ent_next = ADJ[e + 1];
-            const int v = ent & 0x7fffu;
-            const float mo = (float)(ent >> 15);
-            const float2 xl = XY[v];
-            const float dx = xl.x - xj.x, dy = xl.y - xj.y;
-            const float dn = sqrt_approx(fmaf(dx, dx, dy * dy));
-            const f2_t dn2 = f2_pack(dn, dn);
-            f2_t po[D / 2], pi[D / 2];
+        // messages: with q = pb + We_|d| |d|, relu(pa + q) = max(q, -pa) + pa, so the loops sum
+        // max(q, -pa) and (messages) * pa is added after them; each node lists its unknown
+        // neighbours (out- and in-messages) before its halo neighbours (in-messages only), with the
+        // edge length precomputed; the next entry is loaded one iteration ahead
+        {
+            const uint2 *ap = ADJX + e0, *const ae = ADJX + e1, *const au = ADJX + e0 + n_out;
+            uint2 nxt = ap < ae ? *ap : make_uint2(0u, 0u);
+            for (; ap < au; ++ap) {
+                const uint2 ent = nxt;
+                if (ap + 1 < ae) nxt = ap[1];
+                const float dn = __uint_as_float(ent.y);
+                const f2_t dn2 = f2_pack(dn, dn);
+                const float4 *pb = Pb + (size_t)ent.x * 5;
 #pragma unroll
-            for (int m = 0; m < D / 2; ++m) {  // one 16-byte shared load per output pair of both messages
-                const float4 t = Pb[(size_t)v * 5 + m];
-                po[m] = f2_pack(t.x, t.y);
-                pi[m] = f2_pack(t.z, t.w);
+                for (int m = 0; m < D / 2; ++m) {  // one 16-byte shared load per output pair of both messages
+                    const float4 t = pb[m];
+                    so[m] = f2_add(so[m], f2_max_neg(f2_fma(Wp[(F_WEO + 2 * D) / 2 + m], dn2, f2_pack(t.x, t.y)), pao[m]));
+                    if (inner)
+                        si[m] = f2_add(si[m],
+                                       f2_max_neg(f2_fma(Wp[(F_WEI + 2 * D) / 2 + m], dn2, f2_pack(t.z, t.w)), pai[m]));
+                }
             }
-            f2_msg_n<F_WEO, true>(so, pao, po, Wp, dn2, f2_pack(mo, mo));
-            if (inner) f2_msg_n<F_WEI, false>(si, pai, pi, Wp, dn2, 0ull);
+            if (inner) {
+                for (; ap < ae; ++ap) {
+                    const uint2 ent = nxt;
+                    if (ap + 1 < ae) nxt = ap[1];
+                    const float dn = __uint_as_float(ent.y);
+                    const f2_t dn2 = f2_pack(dn, dn);
+                    const float4 *pb = Pb + (size_t)ent.x * 5;
+#pragma unroll
+                    for (int m = 0; m < D / 2; ++m) {
+                        const float4 t = pb[m];
+                        si[m] = f2_add(si[m],
+                                       f2_max_neg(f2_fma(Wp[(F_WEI + 2 * D) / 2 + m], dn2, f2_pack(t.z, t.w)), pai[m]));
+                    }
+                }
+            }
+            const float fi = inner ? (float)(e1 - e0) : 0.f;
+            const f2_t fo2 = f2_pack(dout, dout), fi2 = f2_pack(fi, fi);
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) {
+                so[m] = f2_fma(fo2, pao[m], so[m]);
+                si[m] = f2_fma(fi2, pai[m], si[m]);
+            }
         }
         const float din = inner ? (float)(e1 - e0) : 0.f;
         // Psi hidden layer on [h, c, phi_out, phi_in] with the second message layers composed in
@@ -1612,15 +1646,15 @@ int32_t chunk_build_global(ddg_problem *p, int T, bool tc) {
     }
     DDG_TRY(dalloc(c, cp.allocs, &cp.need, tn));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj, ta));
-    if (tc) DDG_TRY(dalloc(c, cp.allocs, &cp.adjx, ta));
+    DDG_TRY(dalloc(c, cp.allocs, &cp.adjx, ta));
     DDG_TRY(dalloc(c, cp.allocs, &cp.adj_ptr, tp));
     DDG_CU(cudaMemcpyAsync(cp.c_need_off, noff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_adj_off, aoff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     DDG_CU(cudaMemcpyAsync(cp.c_adj_base, abase.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     k_gchunk_build<<<nc, 256, 0, s>>>(cp.c_n0, cp.c_own, cp.gid, p->loc_ptr, p->loc_nint, p->nbr_ptr, p->nbr_off,
                                       p->nbr, p->sub_ptr, p->sub_idx, 1, nullptr, nullptr, cp.c_need_off, cp.need,
-                                      cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->loc_xy,
-                                      tc ? cp.adjx : nullptr, p->d_status);
+                                      cp.c_adj_off, cp.adj_ptr, cp.c_adj_base, cp.adj, cp.info, p->loc_xy, cp.adjx,
+                                      p->d_status);
     DDG_LAUNCH_CHECK();
     DDG_CU(cudaStreamSynchronize(s));
     return check_status(p, "GNN chunks");
@@ -1694,6 +1728,8 @@ int32_t dss_chunk_launch(ddg_problem *p, const double *r, const int *stop, cudaS
     const ChunkPlan &cp = p->chunk;
     const ChunkArgs a = chunk_args(p, r, stop);
     if (p->dss_sched == 5) return dss_d_launch(p, a, s);
+    if (p->dss_sched == 6)
+        return dss_mma_launch(p, a, w_fused_host(p), p->w_bf16 ? p->bf16_mma_dev : p->model->mma_w, s);
     if (cp.tc) return dss_tc_launch(p, a, w_fused_host(p), p->w_bf16 ? p->bf16_tc_dev : p->model->tc_w, s);
     if (cp.global) {
         switch (cp.T) {

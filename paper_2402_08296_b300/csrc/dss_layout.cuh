@@ -193,6 +193,16 @@ __device__ __forceinline__ f2_t f2_relu(f2_t v) {
     return f2_pack(relu(lo), relu(hi));
 }
 
+// max(q, -a) lane by lane; a NaN in either stays NaN (max.NaN)
+__device__ __forceinline__ f2_t f2_max_neg(f2_t q, f2_t a) {
+    float q0, q1, a0, a1, r0, r1;
+    f2_unpack(q, q0, q1);
+    f2_unpack(a, a0, a1);
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r0) : "f"(q0), "f"(-a0));
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r1) : "f"(q1), "f"(-a1));
+    return f2_pack(r0, r1);
+}
+
 // square root by the hardware approximation (relative error near one ulp)
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;

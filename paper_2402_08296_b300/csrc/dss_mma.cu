@@ -1,0 +1,502 @@
+// Schedule 6 of the batched Deep Statistical Solver inference (Section III-B, Eqs. 18-22): the
+// chunks of schedule 4 (at most 128 own and 256 needed nodes, each own node's unknown
+// neighbours first, edge lengths precomputed), one thread per own node as in schedule 3, and
+// every per-node matrix product on the tensor cores as warp-synchronous MMAs
+// (mma.sync m16n8k8, TF32 with the three-term split): a warp multiplies the 32 rows of its
+// nodes at once, so that the products need neither tensor memory nor a CTA-wide wait.
+//
+// Per block, a CTA of 128 threads loops over chunks:
+//   phase A (every needed node, rows of 32 per warp): [h, x, y] -> the neighbour projections
+//     Wb h + We_xy x of both edge MLPs (Eqs. 18-19), written from the MMA fragments straight
+//     into shared memory in the interleaved order the edge loop reads;
+//   phase B (own nodes): [h, x, y, c, d_out, d_in, 1] -> pa_out, pa_in and the h, c, degree
+//     part of Psi's hidden layer (Eq. 20); the edge loop on the CUDA cores
+//     (S = sum of max(pb + We_|d| |d|, -pa), plus (messages) * pa); [S_out, S_in] -> the rest
+//     of the hidden layer (the message MLPs' second layers composed into Psi's first); then
+//     [relu(hidden), 1] -> alpha (Psi_W2 relu + Psi_b2), the residual update h += ...; the
+//     decoder (Eq. 22) of the last block on the CUDA cores.
+// A product goes through the warp's own shared-memory rows: each lane writes its node's input
+// row, the MMA fragments are read from the rows, and the output fragments are written back as
+// rows for each lane to read its node's outputs.  The weights of a block come as MMA B
+// fragments (high and low TF32 parts) in one bulk copy per CTA and launch.  FP32 accuracy from
+// the TF32 units by x W = x_hi W_hi + x_lo W_hi + x_hi W_lo, up to terms below 2^-20 relative
+// (x_hi, W_hi the FP32 values with the low 13 bits cleared, x_lo = x - x_hi, W_lo = W - W_hi).
+#include "dss_layout.cuh"
+
+#include <cstring>
+
+namespace ddg {
+
+// ---------------------------------------------------------------- products and weight image
+// product g: K inputs (a multiple of 8), N outputs (a multiple of 8); fragment image of B = W^T
+// per (k-step, n-tile, lane) {b0_hi, b1_hi, b0_lo, b1_lo} with b0 = W[n0 + g][k0 + t],
+// b1 = W[n0 + g][k0 + t + 4], g = lane / 4, t = lane % 4
+constexpr int MG_K0 = 16, MG_N0 = 24;  // phase A: [h, x, y, 0..] -> 20 projections
+constexpr int MG_K1 = 16, MG_N1 = 32;  // [h, x, y, c, d_out, d_in, 1] -> pa_out, pa_in, hidden part
+constexpr int MG_K2 = 24, MG_N2 = 16;  // [S_out, S_in, 0..] -> hidden increment
+constexpr int MG_K3 = 16, MG_N3 = 16;  // [relu(hidden), 1, 0..] -> alpha (Psi_W2 relu + Psi_b2)
+constexpr int mg_floats(int K, int N) { return (K / 8) * (N / 8) * 32 * 4; }
+constexpr int MG_OFF0 = 0;
+constexpr int MG_OFF1 = MG_OFF0 + mg_floats(MG_K0, MG_N0);  // 768
+constexpr int MG_OFF2 = MG_OFF1 + mg_floats(MG_K1, MG_N1);  // 1792
+constexpr int MG_OFF3 = MG_OFF2 + mg_floats(MG_K2, MG_N2);  // 2560
+static_assert(MG_OFF3 + mg_floats(MG_K3, MG_N3) == MMA_W_FLOATS, "weight image size");
+static_assert((MMA_W_FLOATS * 4) % 16 == 0, "the image is one bulk copy of whole 16-byte pieces");
+
+static float tf32_hi(float w) {
+    uint32_t b;
+    std::memcpy(&b, &w, 4);
+    b &= 0xffffe000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+// W given as a function (output n, input k) -> weight
+template <class F>
+static void put_frag(float *img, int K, int N, F w) {
+    for (int kt = 0; kt < K / 8; ++kt)
+        for (int nt = 0; nt < N / 8; ++nt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                const float b0 = w(nt * 8 + g, kt * 8 + t), b1 = w(nt * 8 + g, kt * 8 + t + 4);
+                float *o = img + (((size_t)kt * (N / 8) + nt) * 32 + lane) * 4;
+                o[0] = tf32_hi(b0);
+                o[1] = tf32_hi(b1);
+                o[2] = b0 - tf32_hi(b0);
+                o[3] = b1 - tf32_hi(b1);
+            }
+}
+
+// The four products of every block from the composed per-block layout of schedule 3
+// (dss_layout.cuh).  Inputs: product 0 [h 0-9, x 10, y 11]; product 1 [h 0-9, x 10, y 11, c 12,
+// d_out 13, d_in 14, one 15]; product 2 [S_out 0-9, S_in 10-19]; product 3 [relu(hidden) 0-9,
+// one 10].  Outputs: product 0 the projections in shared-memory order (out/in pairs
+// interleaved); product 1 pa_out 0-9, pa_in 10-19, hidden part 20-29; products 2 and 3 0-9.
+void mma_weight_image(const float *fused, int kbar, std::vector<float> &img) {
+    img.assign((size_t)kbar * MMA_W_FLOATS, 0.f);
+    for (int b = 0; b < kbar; ++b) {
+        const float *f = fused + (size_t)b * F_FLOATS;
+        float *o = img.data() + (size_t)b * MMA_W_FLOATS;
+        put_frag(o + MG_OFF0, MG_K0, MG_N0, [&](int n, int k) -> float {
+            if (n >= 2 * D) return 0.f;
+            if (k < D) return f[F_HB + k * 2 * D + n];
+            if (k == 10) return f[F_XB + n];
+            if (k == 11) return f[F_XB + 2 * D + n];
+            return 0.f;
+        });
+        put_frag(o + MG_OFF1, MG_K1, MG_N1, [&](int n, int k) -> float {
+            if (n >= 3 * D) return 0.f;
+            const int blk = n / D, q = n % D;  // 0 pa_out, 1 pa_in, 2 hidden
+            if (k < D) return f[F_HA + k * 3 * D + blk * D + q];
+            if (k == 15) return f[F_BA + blk * D + q];
+            if (blk < 2) {
+                if (k == 10) return f[F_NXA + blk * D + q];
+                if (k == 11) return f[F_NXA + 2 * D + blk * D + q];
+                return 0.f;
+            }
+            if (k == 12) return f[F_VC + q];
+            if (k == 13) return f[F_VO + q];
+            if (k == 14) return f[F_VI + q];
+            return 0.f;
+        });
+        put_frag(o + MG_OFF2, MG_K2, MG_N2, [&](int n, int k) -> float {
+            if (n >= D) return 0.f;
+            if (k < D) return f[F_MO + k * D + n];
+            if (k < 2 * D) return f[F_MI + (k - D) * D + n];
+            return 0.f;
+        });
+        put_frag(o + MG_OFF3, MG_K3, MG_N3, [&](int n, int k) -> float {
+            if (n >= D) return 0.f;
+            if (k < D) return f[F_P2 + k * D + n];
+            if (k == D) return f[F_PB2 + n];
+            return 0.f;
+        });
+    }
+}
+
+// ---------------------------------------------------------------- warp products
+constexpr int MW_STRIDE = 36;  // floats per row of a warp's product rows (32 + 4: conflict-free reads)
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc[m][n] (m: rows 0-15 / 16-31 of the warp, n: 8-output tile) = rows R (32 x K, stride
+// MW_STRIDE) times W, three-term split; fragment layout of m16n8k8: a0 (g, t), a1 (g + 8, t),
+// a2 (g, t + 4), a3 (g + 8, t + 4); c0, c1 (g, 2t, 2t + 1), c2, c3 (g + 8, ...)
+template <int K, int N>
+__device__ __forceinline__ void warp_product(const float *R, const float4 *Wf, int lane, float (&acc)[2][N / 8][4]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < N / 8; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < K / 8; ++kt) {
+        float4 w[N / 8];
+#pragma unroll
+        for (int n = 0; n < N / 8; ++n) w[n] = Wf[(kt * (N / 8) + n) * 32 + lane];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const float *r0 = R + (m * 16 + g) * MW_STRIDE + kt * 8 + t;
+            const float x[4] = {r0[0], r0[8 * MW_STRIDE], r0[4], r0[8 * MW_STRIDE + 4]};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                hi[i] = __float_as_uint(x[i]) & 0xffffe000u;
+                lo[i] = __float_as_uint(x[i] - __uint_as_float(hi[i]));
+            }
+#pragma unroll
+            for (int n = 0; n < N / 8; ++n) {
+                mma_tf32(acc[m][n], hi, __float_as_uint(w[n].x), __float_as_uint(w[n].y));
+                mma_tf32(acc[m][n], lo, __float_as_uint(w[n].x), __float_as_uint(w[n].y));
+                mma_tf32(acc[m][n], hi, __float_as_uint(w[n].z), __float_as_uint(w[n].w));
+            }
+        }
+    }
+}
+
+// the output fragments back into the rows (row = node of the warp, NOUT leading outputs)
+template <int N>
+__device__ __forceinline__ void frag_to_rows(float *R, int lane, const float (&acc)[2][N / 8][4]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < N / 8; ++n) {
+            float *r0 = R + (m * 16 + g) * MW_STRIDE + n * 8 + 2 * t;
+            *reinterpret_cast<float2 *>(r0) = make_float2(acc[m][n][0], acc[m][n][1]);
+            *reinterpret_cast<float2 *>(r0 + 8 * MW_STRIDE) = make_float2(acc[m][n][2], acc[m][n][3]);
+        }
+}
+
+// a lane's row: K values (K a multiple of 4; entries past `n` zero)
+template <int K>
+__device__ __forceinline__ void put_row(float *R, int lane, const float (&v)[K]) {
+    float4 *r = reinterpret_cast<float4 *>(R + lane * MW_STRIDE);
+#pragma unroll
+    for (int c = 0; c < K / 4; ++c) r[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
+// ---------------------------------------------------------------- the kernel
+// shared memory: the weight image; per warp its 32 product rows; the needed nodes' projections
+constexpr int MM_T = 128;
+constexpr int MM_OFF_R = MMA_W_FLOATS * 4;                      // 12288
+constexpr int MM_OFF_PB = MM_OFF_R + 4 * 32 * MW_STRIDE * 4;    // 30720
+constexpr int MM_OFF_BAR = MM_OFF_PB + TC_NEED * 80;            // 51200
+constexpr size_t MM_SMEM = MM_OFF_BAR + 16;
+
+__global__ void __launch_bounds__(MM_T, 4)
+    k_dss_mma(const __grid_constant__ FusedWeights W, const __grid_constant__ ChunkArgs a, const float *wimg,
+              int nchunks) {
+    extern __shared__ __align__(16) unsigned char msm[];
+    if (a.stop && *a.stop) return;
+    const float4 *Wf = reinterpret_cast<const float4 *>(msm);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *R = reinterpret_cast<float *>(msm + MM_OFF_R) + warp * 32 * MW_STRIDE;
+    float4 *Pb = reinterpret_cast<float4 *>(msm + MM_OFF_PB);
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(msm + MM_OFF_BAR);
+    const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
+    const float4 *rows = reinterpret_cast<const float4 *>(a.h_in);
+    const bool first = a.first != 0, last = a.last != 0;
+    if (tid == 0) {
+        mbar_init(wbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bulk_load(msm, wimg, MMA_W_FLOATS * 4, wbar);  // set-up data: fetched before the previous block ends
+    }
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the weight copy: every thread waits (bounded); a timeout leaves the launch without work
+    const bool wok = __syncthreads_and(mbar_wait(wbar, 0) ? 1 : 0) != 0;
+    if (!wok) {
+        if (tid == 0) raise_status(a.status, ST_TIMEOUT);
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        return;
+    }
+    f2_t wdo[D / 2], wdi[D / 2];
+#pragma unroll
+    for (int m = 0; m < D / 2; ++m) {
+        wdo[m] = Wp[(F_WEO + 2 * D) / 2 + m];
+        wdi[m] = Wp[(F_WEI + 2 * D) / 2 + m];
+    }
+
+    for (int q = blockIdx.x; q < nchunks; q += gridDim.x) {
+        const int own = a.c_own[q];
+        const int nn = a.c_need_n[q];
+        const int *need = a.need + a.c_need_off[q];
+        // ---- phase A: projections of every needed node, 32 rows per warp and pass
+        for (int base = warp * 32; base < nn; base += MM_T) {
+            const int u = base + lane;
+            float v[MG_K0];
+#pragma unroll
+            for (int o = 0; o < MG_K0; ++o) v[o] = 0.f;
+            if (u < nn) {
+                const int node = need[u];
+                const float2 xy = a.loc_xy[node];
+                if (!first) {
+                    const float4 r0 = rows[3 * (size_t)node], r1 = rows[3 * (size_t)node + 1],
+                                 r2 = rows[3 * (size_t)node + 2];
+                    v[0] = r0.x; v[1] = r0.y; v[2] = r0.z; v[3] = r0.w;
+                    v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w;
+                    v[8] = r2.x; v[9] = r2.y;
+                }
+                v[10] = xy.x;
+                v[11] = xy.y;
+            }
+            put_row<MG_K0>(R, lane, v);
+            __syncwarp();
+            float acc[2][MG_N0 / 8][4];
+            warp_product<MG_K0, MG_N0>(R, Wf + MG_OFF0 / 4, lane, acc);
+            {
+                const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int uu = base + m * 16 + g + 8 * hh;
+                        if (uu >= nn) continue;
+                        float *pr = reinterpret_cast<float *>(Pb + (size_t)uu * 5);
+#pragma unroll
+                        for (int n = 0; n < MG_N0 / 8; ++n) {
+                            const int col = n * 8 + 2 * t;
+                            if (col < 2 * D)
+                                *reinterpret_cast<float2 *>(pr + col) =
+                                    make_float2(acc[m][n][2 * hh], acc[m][n][2 * hh + 1]);
+                        }
+                    }
+            }
+            __syncwarp();  // the rows are read before the next pass writes them
+        }
+        __syncthreads();
+        // ---- phase B: own nodes (warps with at least one)
+        if (warp * 32 < own) {
+            const int u = tid;
+            const bool mine = u < own;
+            int4 inf = make_int4(0, -1, 0, 0);
+            int e0 = 0, e1 = 0;
+            float h[D], c = 0.f, v[MG_K1];
+#pragma unroll
+            for (int o = 0; o < D; ++o) h[o] = 0.f;
+#pragma unroll
+            for (int o = 0; o < MG_K1; ++o) v[o] = 0.f;
+            bool inner = false;
+            if (mine) {
+                inf = a.info[a.c_n0[q] + u];
+                inner = inf.y >= 0;
+                const int *aptr = a.adj_ptr + a.c_adj_off[q];
+                e0 = aptr[u];
+                e1 = aptr[u + 1];
+                const int node = inf.x;
+                const float2 xy = a.loc_xy[node];
+                if (first) {
+                    const double s = a.s[inf.w & 0xffffff];
+                    c = (inner && s != 0.0) ? (float)(a.r[inf.z] / s) : 0.f;
+                } else {
+                    load_hrow(rows, node, h, c);
+                }
+#pragma unroll
+                for (int o = 0; o < D; ++o) v[o] = h[o];
+                v[10] = xy.x;
+                v[11] = xy.y;
+                v[12] = c;
+                v[13] = (float)((unsigned)inf.w >> 24);
+                v[14] = inner ? (float)(e1 - e0) : 0.f;
+                v[15] = 1.f;
+            }
+            put_row<MG_K1>(R, lane, v);
+            __syncwarp();
+            f2_t pao[D / 2], pai[D / 2];
+            float hid[D];
+            {
+                float acc[2][MG_N1 / 8][4];
+                warp_product<MG_K1, MG_N1>(R, Wf + MG_OFF1 / 4, lane, acc);
+                __syncwarp();
+                frag_to_rows<MG_N1>(R, lane, acc);
+                __syncwarp();
+                const float4 *r = reinterpret_cast<const float4 *>(R + lane * MW_STRIDE);
+                float o[32];
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    const float4 x = r[cc];
+                    o[4 * cc] = x.x; o[4 * cc + 1] = x.y; o[4 * cc + 2] = x.z; o[4 * cc + 3] = x.w;
+                }
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    pao[m] = f2_pack(o[2 * m], o[2 * m + 1]);
+                    pai[m] = f2_pack(o[D + 2 * m], o[D + 2 * m + 1]);
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) hid[k] = o[2 * D + k];
+            }
+            // ---- edge messages: S = sum max(pb + We_|d| |d|, -pa), unknown neighbours first
+            f2_t so[D / 2], si[D / 2];
+#pragma unroll
+            for (int m = 0; m < D / 2; ++m) so[m] = si[m] = 0ull;
+            if (mine) {
+                const int n_out = min((int)((unsigned)inf.w >> 24), e1 - e0);
+                const uint2 *adj = a.adjx + a.c_adj_base[q];
+                const uint2 *ap = adj + e0, *const ae = adj + e1, *const au = adj + e0 + n_out;
+                uint2 nxt = ap < ae ? *ap : make_uint2(0u, 0u);
+                for (; ap < au; ++ap) {
+                    const uint2 ent = nxt;
+                    if (ap + 1 < ae) nxt = ap[1];
+                    const float dn = __uint_as_float(ent.y);
+                    const f2_t dn2 = f2_pack(dn, dn);
+                    const float4 *pb = Pb + (size_t)ent.x * 5;
+#pragma unroll
+                    for (int m = 0; m < D / 2; ++m) {
+                        const float4 t4 = pb[m];
+                        so[m] = f2_add(so[m], f2_max_neg(f2_fma(wdo[m], dn2, f2_pack(t4.x, t4.y)), pao[m]));
+                        if (inner) si[m] = f2_add(si[m], f2_max_neg(f2_fma(wdi[m], dn2, f2_pack(t4.z, t4.w)), pai[m]));
+                    }
+                }
+                if (inner) {
+                    for (; ap < ae; ++ap) {
+                        const uint2 ent = nxt;
+                        if (ap + 1 < ae) nxt = ap[1];
+                        const float dn = __uint_as_float(ent.y);
+                        const f2_t dn2 = f2_pack(dn, dn);
+                        const float4 *pb = Pb + (size_t)ent.x * 5;
+#pragma unroll
+                        for (int m = 0; m < D / 2; ++m) {
+                            const float4 t4 = pb[m];
+                            si[m] = f2_add(si[m], f2_max_neg(f2_fma(wdi[m], dn2, f2_pack(t4.z, t4.w)), pai[m]));
+                        }
+                    }
+                }
+                const float fo = (float)n_out, fi = inner ? (float)(e1 - e0) : 0.f;
+                const f2_t fo2 = f2_pack(fo, fo), fi2 = f2_pack(fi, fi);
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    so[m] = f2_fma(fo2, pao[m], so[m]);
+                    si[m] = f2_fma(fi2, pai[m], si[m]);
+                }
+            }
+            // ---- hidden += (Psi_W1 W2_out) S_out + (Psi_W1 W2_in) S_in
+            {
+                float w2[MG_K2];
+#pragma unroll
+                for (int m = 0; m < D / 2; ++m) {
+                    f2_unpack(so[m], w2[2 * m], w2[2 * m + 1]);
+                    f2_unpack(si[m], w2[D + 2 * m], w2[D + 2 * m + 1]);
+                }
+#pragma unroll
+                for (int o = 2 * D; o < MG_K2; ++o) w2[o] = 0.f;
+                __syncwarp();
+                put_row<MG_K2>(R, lane, w2);
+                __syncwarp();
+                float acc[2][MG_N2 / 8][4];
+                warp_product<MG_K2, MG_N2>(R, Wf + MG_OFF2 / 4, lane, acc);
+                __syncwarp();
+                frag_to_rows<MG_N2>(R, lane, acc);
+                __syncwarp();
+                const float4 *r = reinterpret_cast<const float4 *>(R + lane * MW_STRIDE);
+                const float4 x0 = r[0], x1 = r[1], x2 = r[2];
+                const float inc[D] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y};
+#pragma unroll
+                for (int k = 0; k < D; ++k) hid[k] += inc[k];
+            }
+            // ---- h += alpha (Psi_W2 relu(hidden) + Psi_b2)
+            float hn[D];
+            {
+                float w3[MG_K3];
+#pragma unroll
+                for (int k = 0; k < D; ++k) w3[k] = relu(hid[k]);
+                w3[D] = 1.f;
+#pragma unroll
+                for (int o = D + 1; o < MG_K3; ++o) w3[o] = 0.f;
+                __syncwarp();
+                put_row<MG_K3>(R, lane, w3);
+                __syncwarp();
+                float acc[2][MG_N3 / 8][4];
+                warp_product<MG_K3, MG_N3>(R, Wf + MG_OFF3 / 4, lane, acc);
+                __syncwarp();
+                frag_to_rows<MG_N3>(R, lane, acc);
+                __syncwarp();
+                const float4 *r = reinterpret_cast<const float4 *>(R + lane * MW_STRIDE);
+                const float4 x0 = r[0], x1 = r[1], x2 = r[2];
+                const float dh[D] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y};
+#pragma unroll
+                for (int k = 0; k < D; ++k) hn[k] = h[k] + dh[k];
+            }
+            if (mine) {
+                if (last) {
+                    if (inner) {
+                        f2_t dd[D / 2];
+#pragma unroll
+                        for (int m = 0; m < D / 2; ++m) dd[m] = Wp[F_DB1 / 2 + m];
+                        f2_mv<F_DW1, D>(dd, Wp, hn);
+                        float y = W.w[F_DB2];
+#pragma unroll
+                        for (int m = 0; m < D / 2; ++m) {
+                            float d0, d1;
+                            f2_unpack(dd[m], d0, d1);
+                            y = fmaf(W.w[F_DW2 + 2 * m], relu(d0), y);
+                            y = fmaf(W.w[F_DW2 + 2 * m + 1], relu(d1), y);
+                        }
+                        const double s = a.s[inf.w & 0xffffff];
+                        a.corr[inf.y] = s == 0.0 ? 0.0 : s * (double)y;
+                    }
+                } else {
+                    float4 *hrow_out = reinterpret_cast<float4 *>(a.h_out) + 3 * (size_t)inf.x;
+                    hrow_out[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+                    hrow_out[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
+                    hrow_out[2] = make_float4(hn[8], hn[9], c, 0.f);
+                }
+            }
+        }
+        __syncthreads();  // the projections are read before the next chunk writes them
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+static int32_t mma_configure(int *per_sm) {
+    static bool configured = false;
+    if (!configured) {
+        DDG_CU(cudaFuncSetAttribute(k_dss_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MM_SMEM));
+        configured = true;
+    }
+    DDG_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dss_mma, MM_T, MM_SMEM));
+    return DDG_OK;
+}
+
+int32_t mma_ctas_per_sm(int *out) { return mma_configure(out); }
+
+int32_t dss_mma_launch(ddg_problem *p, const ChunkArgs &base, const float *fused_host, const float *mma_w,
+                       cudaStream_t s) {
+    int per_sm = 0, sms = 0;
+    DDG_TRY(mma_configure(&per_sm));
+    DDG_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->ctx->device));
+    const ddg_model *m = p->model;
+    const int nc = p->chunk.nchunks;
+    const int grid = std::max(1, std::min(nc, sms * std::max(1, per_sm)));
+    for (int blk = 0; blk < m->kbar; ++blk) {
+        ChunkArgs a = base;
+        a.first = blk == 0;
+        a.last = blk == m->kbar - 1;
+        a.h_in = (blk & 1) ? p->dss_h2 : p->dss_h;
+        a.h_out = (blk & 1) ? p->dss_h : p->dss_h2;
+        const FusedWeights *Wb = reinterpret_cast<const FusedWeights *>(fused_host) + blk;
+        const float *img = mma_w + (size_t)blk * MMA_W_FLOATS;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(MM_T);
+        cfg.dynamicSmemBytes = MM_SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = p->ctx->pdl ? 1 : 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DDG_CU(cudaLaunchKernelEx(&cfg, k_dss_mma, *Wb, a, img, nc));
+    }
+    DDG_LAUNCHES(m->kbar);
+    return DDG_OK;
+}
+
+}  // namespace ddg

@@ -216,10 +216,11 @@ int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s
 // per block, one CTA per graph, weights in the constant bank; 2 = as 1 with
 // the graphs cut into chunks of at most 2T nodes (T = 128, 192, 256); 3 = the
 // chunks of 2 with composed weights, packed two-lane FP32 and message-sorted nodes;
-// 4 = chunks of at most 128 nodes with the per-node matrix products of the latent
-// vectors on the tensor cores (dss_tc.cu); 5 = the generic kernel for any latent size
-// d in {5, 10, 20} (dss_d.cu), the only schedule for d != 10.
-// DDG_GNN_SCHEDULE = 0..4 (and DDG_GNN_CHUNK_T = 128/192/256 for schedule 2,
+// 4 = chunks of at most 128 own nodes with the per-node matrix products on the tensor
+// cores through tensor memory (tcgen05, dss_tc.cu); 5 = the generic kernel for any latent
+// size d in {5, 10, 20} (dss_d.cu), the only schedule for d != 10; 6 = schedule 4's chunks
+// with the per-node products as warp-synchronous tensor-core MMAs (dss_mma.cu).
+// DDG_GNN_SCHEDULE = 0..6 (and DDG_GNN_CHUNK_T = 128/192/256 for schedule 2,
 // 128/256 for schedule 3) forces one.
 // The choice is cached in the context per decomposition shape class, so a stream
 // of requests of similar sizes tunes once.
@@ -231,7 +232,7 @@ int32_t dss_autotune(ddg_problem *p) {
         p->dss_sched = 5;
         return chunk_build(p, DSS_D_CHUNK_T);
     }
-    if (env && env[0] >= '0' && env[0] <= '4' && env[1] == 0) {
+    if (env && ((env[0] >= '0' && env[0] <= '4') || env[0] == '6') && env[1] == 0) {
         p->dss_sched = env[0] - '0';
         if (p->dss_sched < 2 && !p->dss_whole_graph) {
             set_error("GNN schedules 0 and 1 need every local graph in one CTA; use 2 or 3");
@@ -239,7 +240,7 @@ int32_t dss_autotune(ddg_problem *p) {
         }
         if (p->dss_sched == 2) DDG_TRY(chunk_build(p, envT ? atoi(envT) : 192));
         if (p->dss_sched == 3) DDG_TRY(chunk_build_global(p, envT ? atoi(envT) : 128, false));
-        if (p->dss_sched == 4) DDG_TRY(chunk_build_global(p, TC_T, true));
+        if (p->dss_sched == 4 || p->dss_sched == 6) DDG_TRY(chunk_build_global(p, TC_T, true));
         return DDG_OK;
     }
     const long long cls_K = (long long)std::floor(4.0 * std::log2((double)p->K));
@@ -259,7 +260,7 @@ int32_t dss_autotune(ddg_problem *p) {
             p->dss_sched = cached;
             if (cached == 2) DDG_TRY(chunk_build(p, cachedT));
             if (cached == 3) DDG_TRY(chunk_build_global(p, cachedT, false));
-            if (cached == 4) DDG_TRY(chunk_build_global(p, TC_T, true));
+            if (cached == 4 || cached == 6) DDG_TRY(chunk_build_global(p, TC_T, true));
             return DDG_OK;
         }
     }
@@ -269,12 +270,13 @@ int32_t dss_autotune(ddg_problem *p) {
     DDG_CU(cudaEventCreate(&e1));
     float best = 1e30f;
     int pick = 0, pickT = 0;
-    const int cands[8][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}, {3, 128}, {3, 256}, {4, TC_T}};
+    const int cands[9][2] = {{0, 0}, {1, 0}, {2, 128}, {2, 192}, {2, 256}, {3, 128}, {3, 256}, {4, TC_T}, {6, TC_T}};
     for (const auto &cd : cands) {
         if (cd[0] < 2 && !p->dss_whole_graph) continue;
         p->dss_sched = cd[0];
         if (cd[0] == 2) DDG_TRY(chunk_build(p, cd[1]));
-        if (cd[0] >= 3) DDG_TRY(chunk_build_global(p, cd[1], cd[0] == 4));
+        if (cd[0] == 3) DDG_TRY(chunk_build_global(p, cd[1], false));
+        if (cd[0] >= 4 && !p->chunk.tc) DDG_TRY(chunk_build_global(p, cd[1], true));  // 4 and 6 share one plan
         DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
         DDG_CU(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 2; ++rep) DDG_TRY(precond_core(p, p->b, nullptr, s, nullptr, false));
@@ -292,8 +294,8 @@ int32_t dss_autotune(ddg_problem *p) {
     cudaEventDestroy(e1);
     p->dss_sched = pick;
     if (pick >= 2) {
-        if (p->chunk.T != pickT || p->chunk.global != (pick >= 3) || p->chunk.tc != (pick == 4))
-            DDG_TRY(pick >= 3 ? chunk_build_global(p, pickT, pick == 4) : chunk_build(p, pickT));
+        if (p->chunk.T != pickT || p->chunk.global != (pick >= 3) || p->chunk.tc != (pick >= 4))
+            DDG_TRY(pick >= 3 ? chunk_build_global(p, pickT, pick >= 4) : chunk_build(p, pickT));
     } else {
         chunk_free(p);
     }

@@ -11,7 +11,7 @@ from helpers import assert_close, gpu_setup, oracle_setup, rel
 pytestmark = pytest.mark.gpu
 
 KBAR, D = 30, 10
-SCHEDULES = [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256"), ("4", None)]
+SCHEDULES = [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256"), ("4", None), ("6", None)]
 
 
 @pytest.fixture(scope="module")

@@ -115,7 +115,7 @@ def _sample(D, count=4):
     return sorted(pick)
 
 
-@pytest.mark.parametrize("schedule", ["auto", "3", "4"])
+@pytest.mark.parametrize("schedule", ["auto", "3", "4", "6"])
 def test_full_gnn_corrections_sampled(ddg, ctx, torch, full, schedule, monkeypatch):
     """Sampled subdomains' GNN corrections at the full sizes: the schedule the autotuner picks
     (the benchmark's launch configuration) and the two chunked schedules explicitly."""

@@ -113,7 +113,7 @@ def test_dss_local_corrections(ddg, ctx, torch, name, seed, K, delta, alpha, bia
 
 
 @pytest.mark.parametrize("schedule,chunk_t", [("0", None), ("1", None), ("2", "128"), ("3", "128"), ("3", "256"),
-                                             ("4", None)])
+                                             ("4", None), ("6", None)])
 def test_dss_local_corrections_every_schedule(ddg, ctx, torch, schedule, chunk_t, monkeypatch):
     """Every GNN schedule against the FP64 oracle on ragged ~1,300-node graphs; with
     T = 128 each graph spans several chunks, so chunk borders and halos are exercised."""
@@ -151,7 +151,7 @@ def test_dss_local_corrections_every_schedule(ddg, ctx, torch, schedule, chunk_t
         ddg.ddg_model_destroy(m)
 
 
-@pytest.mark.parametrize("schedule", ["2", "3", "4"])
+@pytest.mark.parametrize("schedule", ["2", "3", "4", "6"])
 def test_dss_sub_meshes_of_2000_nodes(ddg, ctx, torch, schedule, monkeypatch):
     """Sub-meshes of ~2,000 unknowns (Section V-B's largest N_s) give local graphs beyond one
     CTA; the chunked schedules run them and match the oracle, the whole-graph ones refuse."""
@@ -285,7 +285,7 @@ def test_model_xavier_init_matches_splitmix_stream(ddg, ctx):
         ddg.ddg_model_destroy(m)
 
 
-@pytest.mark.parametrize("schedule", ["auto", "0", "2", "3", "4"])
+@pytest.mark.parametrize("schedule", ["auto", "0", "2", "3", "4", "6"])
 @pytest.mark.parametrize("weights", ["trained", "xavier"])
 def test_dss_kbar_10(ddg, ctx, torch, weights, schedule, monkeypatch):
     """kbar = 10 message-passing blocks (the setting of Fig. 6 with the best wall time): the

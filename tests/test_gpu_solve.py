@@ -147,7 +147,7 @@ def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, monkeypat
     m = ddg.ddg_model_create(ctx, 30, 10, 0.02, W)
     ref = None
     try:
-        for schedule in ["0", "1", "2", "3", "4"]:
+        for schedule in ["0", "1", "2", "3", "4", "6"]:
             monkeypatch.setenv("DDG_GNN_SCHEDULE", schedule)
             monkeypatch.delenv("DDG_NO_GRAPH", raising=False)
             ddg.ddg_setup_precond(p, ddg.DDG_DDM_GNN, m, ddg.DDG_COARSE)
@@ -172,7 +172,7 @@ def test_gnn_schedules_agree_and_graph_replay_matches_direct(ddg, ctx, monkeypat
         ddg.ddg_model_destroy(m)
 
 
-@pytest.mark.parametrize("schedule", ["auto", "3", "4"])
+@pytest.mark.parametrize("schedule", ["auto", "3", "4", "6"])
 def test_ddm_gnn_solve_judged_by_the_oracle(ddg, ctx, schedule, monkeypatch):
     """DDM-GNN FCG(10) with the trained weights to 1e-6 on a ~20k-node star domain: the oracle's
     own assembly gives the true relative residual, and x is within kappa * tol of the oracle's
