@@ -387,8 +387,10 @@ __global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, l
     }
 }
 
-// q = A p with the partial dots p.q and p.r (rows strided over the grid, one row per thread
-// at a time); the last block forms alpha = (p.r) / (p.q)
+// q = A p with the partial dots p.q and p.r, rows strided over the grid (up to eight CTAs per SM,
+// a few rows per thread); the first eight entries of a row are loaded under predicates, so that
+// their loads are all in flight at once, the rest in a loop; the last block forms
+// alpha = (p.r) / (p.q)
 __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
                                                  const double *__restrict__ val, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
@@ -398,8 +400,12 @@ __global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr,
     if (flag[F_STOP]) return;
     double d[2] = {0.0, 0.0};  // p.q, p.r
     for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
+        const int e0 = rowptr[i], len = rowptr[i + 1] - e0;
         double acc = 0.0;
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * p[col[e]];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (e < len) acc += val[e0 + e] * p[col[e0 + e]];
+        for (int e = 8; e < len; ++e) acc += val[e0 + e] * p[col[e0 + e]];
         q[i] = acc;
         const double pi = p[i];
         d[0] += pi * acc;
@@ -634,7 +640,8 @@ struct FcgRun {
             long long g = std::min(std::max((long long)cdiv(nf, KT * 8), (long long)sms), 2LL * sms);
             G = (int)std::max(1LL, std::min(g, (long long)cdiv(nf, KT)));
         }
-        nb_spmv = G;
+        // the SpMV: up to eight CTAs per SM (its block sums are two per CTA)
+        nb_spmv = (int)std::max(1LL, std::min((long long)RB, (long long)cdiv(nf, KT)));
         off_sp = OFF_MD + MAXM * RB;
         off_rr = off_sp + 2LL * nb_spmv;
         use_graph = getenv("DDG_NO_GRAPH") == nullptr && record == nullptr;

@@ -518,27 +518,102 @@ __global__ void __launch_bounds__(CO_T) k_coarse_rows(const int *sub_ptr, const 
     }
 }
 
-__global__ void k_gj_pivot(const double *A, int K, int k, double *prow, double *fcol, int *st) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= K) return;
-    double piv = A[(long long)k * K + k];
-    if (!(piv > 0.0)) {
-        if (j == 0) raise_status(st, ST_BAD_INPUT);
-        return;
+// Inverse of the SPD coarse matrix by blocked Gauss-Jordan elimination, in place, pivot blocks
+// of GJB rows taken in order (no pivoting: every leading block of an SPD matrix and each Schur
+// complement stay SPD).  Step k with the pivot block A_kk and P = A_kk^-1:
+//   A_kj <- P A_kj,  A_ij <- A_ij - A_ik (P A_kj),  A_ik <- -A_ik P  (i, j != k),  A_kk <- P,
+// the block form of the scalar sweep a_kj /= a_kk, a_ij -= a_ik a_kj, a_ik = -a_ik / a_kk,
+// a_kk = 1 / a_kk; after the last step A holds A^-1.  Three launches per step: the pivot
+// block's inverse (one CTA, scalar Gauss-Jordan in shared memory), the panel (P times row
+// block k, and a copy of column block k), and the update of every element from the panel.
+constexpr int GJB = 32;
+
+__global__ void __launch_bounds__(GJB *GJB) k_bgj_pivot(const double *A, int K, int k0, int nb, double *P, int *st) {
+    __shared__ double M[GJB][GJB + 1];
+    __shared__ double prow[GJB], fcol[GJB], rpiv;
+    const int i = threadIdx.y, j = threadIdx.x;
+    M[i][j] = (i < nb && j < nb) ? A[(long long)(k0 + i) * K + k0 + j] : (i == j ? 1.0 : 0.0);
+    __syncthreads();
+    bool bad = false;
+    for (int k = 0; k < nb; ++k) {
+        if (i == 0 && j == 0) {
+            const double piv = M[k][k];
+            bad |= !(piv > 0.0);
+            rpiv = 1.0 / piv;
+        }
+        __syncthreads();
+        if (i == 0) prow[j] = (j == k ? 1.0 : M[k][j]) * rpiv;
+        if (j == 0) fcol[i] = M[i][k];
+        __syncthreads();
+        M[i][j] = (i == k) ? prow[j] : ((j == k ? 0.0 : M[i][j]) - fcol[i] * prow[j]);
+        __syncthreads();
     }
-    prow[j] = (j == k ? 1.0 : A[(long long)k * K + j]) / piv;
-    fcol[j] = A[(long long)j * K + k];
+    P[i * GJB + j] = M[i][j];
+    if (bad) raise_status(st, ST_BAD_INPUT);
 }
 
-__global__ void k_gj_update(double *A, int K, int k, const double *prow, const double *fcol) {
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (long long)K * K) return;
-    int i = (int)(q / K), j = (int)(q % K);
-    if (i == k) {
-        A[q] = prow[j];
-    } else {
-        double aij = (j == k) ? 0.0 : A[q];
-        A[q] = aij - fcol[i] * prow[j];
+// R = P A[k0 .. k0 + nb)[:] (nb x K, row-major), C = A[:][k0 .. k0 + nb) (K x GJB, row-major):
+// 32 columns per CTA, a thread four rows of R in one column and one column's C entries
+__global__ void __launch_bounds__(256) k_bgj_panel(const double *A, int K, int k0, int nb, const double *P,
+                                                   double *R, double *C) {
+    __shared__ double Ps[GJB][GJB + 1], As[GJB][GJB + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int j = blockIdx.x * GJB + tx;
+    for (int rr = ty; rr < GJB; rr += 8) {
+        Ps[rr][tx] = P[rr * GJB + tx];
+        As[rr][tx] = (rr < nb && j < K) ? A[(long long)(k0 + rr) * K + j] : 0.0;
+    }
+    __syncthreads();
+    if (j < K)
+        for (int r = ty; r < nb; r += 8) {
+            double acc = 0.0;
+#pragma unroll 8
+            for (int m = 0; m < GJB; ++m) acc += Ps[r][m] * As[m][tx];
+            R[(long long)r * K + j] = acc;
+        }
+    // column block k of row j (the rows of this CTA's columns, read along the row)
+    for (int rr = ty; rr < GJB; rr += 8) {
+        const int row = blockIdx.x * GJB + rr;
+        if (row < K) C[(long long)row * GJB + tx] = tx < nb ? A[(long long)row * K + k0 + tx] : 0.0;
+    }
+}
+
+// every element from the panel; tiles of 32 x 32, a thread four rows of one column
+__global__ void __launch_bounds__(256) k_bgj_update(double *A, int K, int k0, int nb, const double *P,
+                                                    const double *R, const double *C) {
+    __shared__ double Cs[GJB][GJB + 1], Rs[GJB][GJB + 1], Ps[GJB][GJB + 1];
+    const int i0 = blockIdx.y * GJB, j0 = blockIdx.x * GJB;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const bool col_k = j0 < k0 + nb && j0 + GJB > k0;        // the tile meets column block k
+    for (int rr = ty; rr < GJB; rr += 8) {
+        const int i = i0 + rr, j = j0 + tx;
+        Cs[rr][tx] = i < K ? C[(long long)i * GJB + tx] : 0.0;
+        Rs[rr][tx] = (rr < nb && j < K) ? R[(long long)rr * K + j] : 0.0;
+        if (col_k) Ps[rr][tx] = P[rr * GJB + tx];
+    }
+    __syncthreads();
+    const int j = j0 + tx;
+    if (j >= K) return;
+    const bool in_j = j >= k0 && j < k0 + nb;
+    for (int rr = ty; rr < GJB; rr += 8) {
+        const int i = i0 + rr;
+        if (i >= K) break;
+        const bool in_i = i >= k0 && i < k0 + nb;
+        double v;
+        if (in_i && in_j) {
+            v = Ps[i - k0][j - k0];
+        } else if (in_i) {
+            v = Rs[i - k0][tx];
+        } else if (in_j) {
+            double acc = 0.0;
+            for (int m = 0; m < nb; ++m) acc += Cs[rr][m] * Ps[m][j - k0];
+            v = -acc;
+        } else {
+            double acc = 0.0;
+            for (int m = 0; m < nb; ++m) acc += Cs[rr][m] * Rs[m][tx];
+            v = A[(long long)i * K + j] - acc;
+        }
+        A[(long long)i * K + j] = v;
     }
 }
 
@@ -560,17 +635,23 @@ int32_t coarse_build(ddg_problem *p) {
     DDG_TRY(check_status(p, "coarse matrix"));
     DDG_CU(cudaMemcpyAsync(p->A0inv, p->A0, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
     Scratch sc(s);
-    double *prow, *fcol;
-    DDG_CU(sc.get(&prow, K));
-    DDG_CU(sc.get(&fcol, K));
-    long long KK = (long long)K * K;
-    for (int k = 0; k < K; ++k) {
-        k_gj_pivot<<<cdiv(K, 256), 256, 0, s>>>(p->A0inv, K, k, prow, fcol, p->d_status);
-        k_gj_update<<<cdiv(KK, 256), 256, 0, s>>>(p->A0inv, K, k, prow, fcol);
+    double *Pk, *Rk, *Ck;
+    DDG_CU(sc.get(&Pk, GJB * GJB));
+    DDG_CU(sc.get(&Rk, (size_t)GJB * K));
+    DDG_CU(sc.get(&Ck, (size_t)GJB * K));
+    const dim3 tiles(cdiv(K, GJB), cdiv(K, GJB));
+    int steps = 0;
+    for (int k0 = 0; k0 < K; k0 += GJB, ++steps) {
+        const int nb = std::min(GJB, K - k0);
+        k_bgj_pivot<<<1, dim3(GJB, GJB), 0, s>>>(p->A0inv, K, k0, nb, Pk, p->d_status);
+        k_bgj_panel<<<cdiv(K, GJB), 256, 0, s>>>(p->A0inv, K, k0, nb, Pk, Rk, Ck);
+        k_bgj_update<<<tiles, 256, 0, s>>>(p->A0inv, K, k0, nb, Pk, Rk, Ck);
     }
-    DDG_LAUNCHES(2 * K);
-    DDG_CU(sc.drop(prow));
-    DDG_CU(sc.drop(fcol));
+    DDG_LAUNCH_CHECK();
+    DDG_LAUNCHES(3 * steps);
+    DDG_CU(sc.drop(Pk));
+    DDG_CU(sc.drop(Rk));
+    DDG_CU(sc.drop(Ck));
     DDG_CU(cudaStreamSynchronize(s));
     int32_t r = check_status(p, "coarse inverse");
     if (r == DDG_INVALID_ARG) set_error("coarse matrix A_0 is not positive definite");
