@@ -43,8 +43,9 @@ L2_FLUSH_BYTES = 512 << 20
 GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused", 4: "k_dss_tc", 5: "k_dss_d", 6: "k_dss_mma"}
 # DRAM bytes (read + write) per GNN application from an ncu capture of the current kernel form,
 # keyed by (workload, schedule, chunk width); absent (null in the line) when no capture of the
-# current kernel exists for the workload.  Filled from the committed profiles.
-GNN_TRAFFIC: dict = {}
+# current kernel exists for the workload.  From profiles/k_dss_fused_star1m.md: first block
+# 152.6 MB, each of the 28 middle blocks 222.3 MB, last block 185.6 MB.
+GNN_TRAFFIC: dict = {("star1m", 3, 256): int(152.6e6 + 28 * 222.3e6 + 185.6e6)}
 # FCG iterations of the GPU path with the committed weights (the reference arm's scale)
 GNN_ITERATIONS = {"star1m": 78, "star100k": 70}
 

@@ -175,6 +175,12 @@ struct ddg_problem {
     int nnz = 0;
     int *rowptr = nullptr, *col = nullptr;
     double *val = nullptr, *b = nullptr;
+    // the same matrix in sliced ELLPACK for the SpMV (krylov.cu): slices of 32 rows, rows sorted
+    // by decreasing length within windows of 256; slot k holds row sl_perm[k]; entry e of the
+    // slot's row at sl_ptr[k / 32] + 32 e + k % 32 (padding: column = the row, value 0)
+    int n_slices = 0;
+    int *sl_perm = nullptr, *sl_len = nullptr, *sl_ptr = nullptr, *sl_col = nullptr;
+    double *sl_val = nullptr;
     double *g = nullptr;       // [n] Dirichlet values (0 on free nodes)
     double bnorm = 0.0;
     ddg::Allocs a_matrix;
@@ -305,6 +311,7 @@ int32_t lu_build(ddg_problem *p);
 int32_t precond_apply(ddg_problem *p, const double *r, double *z, cudaStream_t s, bool corrections_only,
                       double *corr_out, double *s_out);
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s);
+int32_t sell_build(ddg_problem *p);  // the sliced ELLPACK copy of A_ff (after assembly)
 int32_t model_pack(ddg_model *m);
 int32_t model_host_layouts(ddg_model *m);
 int32_t dss_select_weights(ddg_problem *p, bool bf16);  // rebuilds packed_host and fused_host from the device flat weights

@@ -61,21 +61,112 @@ __device__ __forceinline__ void block_parts(const double (&v)[NV], int nv, doubl
 }
 
 // ------------------------------------------------------------------ SpMV
-// y_i = sum_e val[e] x[col[e]], one row per thread in CSR order.  (A shared-memory tiled form
-// and an eight-lanes-per-row form both measured slower: with ~7 nonzeros per row the L1 serves
-// the row-per-thread reuse, and the FP64 units bound these kernels on this part.)
-__global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ col,
-                                             const double *__restrict__ val, const double *__restrict__ x,
-                                             double *__restrict__ y, int n) {
-    const int i = blockIdx.x * KT + threadIdx.x;
-    if (i >= n) return;
+// The fine operator runs on a sliced ELLPACK copy of the CSR matrix: slices of SL_W = 32 rows,
+// one warp per slice, entry e of every row of the slice stored side by side, so that each load
+// of the warp is one contiguous 256-byte (values) or 128-byte (columns) access.  Rows are sorted
+// by decreasing length within windows of SL_WIN rows before they are cut into slices, so that
+// the rows of a slice have nearly equal lengths (padding of a few per cent on a triangle mesh);
+// padding entries hold the row itself as column and 0 as value.  Entries keep the CSR order
+// within a row, so y_i sums the same products in the same order as a CSR row loop.
+constexpr int SL_W = 32, SL_WIN = 256;
+
+// one CTA per window: rank of every row by (decreasing length, increasing index), the window's
+// slot order and the length of each slice (its first, longest row)
+__global__ void __launch_bounds__(SL_WIN) k_sell_order(const int *rowptr, int n, int *perm, int *slice_len) {
+    __shared__ int len[SL_WIN], sorted[SL_WIN];
+    const int w0 = blockIdx.x * SL_WIN, cnt = min(SL_WIN, n - w0), t = threadIdx.x;
+    len[t] = t < cnt ? rowptr[w0 + t + 1] - rowptr[w0 + t] : -1;
+    __syncthreads();
+    if (t < cnt) {
+        const int lt = len[t];
+        int rank = 0;
+        for (int u = 0; u < cnt; ++u) rank += (len[u] > lt || (len[u] == lt && u < t)) ? 1 : 0;
+        perm[w0 + rank] = w0 + t;
+        sorted[rank] = lt;
+    }
+    __syncthreads();
+    if (t < SL_WIN / SL_W && t * SL_W < cnt) slice_len[w0 / SL_W + t] = sorted[t * SL_W];
+}
+
+// 32 * slice length per slice (the scan's input)
+__global__ void k_sell_sizes(const int *slice_len, int ns, int *sz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ns) sz[i] = SL_W * slice_len[i];
+}
+
+__global__ void k_sell_fill(const int *rowptr, const int *col, const double *val, const int *perm,
+                            const int *slice_len, const int *slice_ptr, int n, int *scol, double *sval) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int row = perm[k], e0 = rowptr[row], len = rowptr[row + 1] - e0;
+    const int base = slice_ptr[k / SL_W] + (k % SL_W), L = slice_len[k / SL_W];
+    for (int e = 0; e < L; ++e) {
+        scol[base + SL_W * e] = e < len ? col[e0 + e] : row;
+        sval[base + SL_W * e] = e < len ? val[e0 + e] : 0.0;
+    }
+}
+
+int32_t sell_build(ddg_problem *p) {
+    ddg_ctx *c = p->ctx;
+    cudaStream_t s = p->stream;
+    const int n = p->nf;
+    const int ns = cdiv(n, SL_W);
+    p->n_slices = ns;
+    DDG_TRY(dalloc(c, p->a_matrix, &p->sl_perm, std::max(n, 1)));
+    DDG_TRY(dalloc(c, p->a_matrix, &p->sl_len, ns + 1));
+    DDG_TRY(dalloc(c, p->a_matrix, &p->sl_ptr, ns + 1));
+    if (n == 0) return DDG_OK;
+    k_sell_order<<<cdiv(n, SL_WIN), SL_WIN, 0, s>>>(p->rowptr, n, p->sl_perm, p->sl_len);
+    k_sell_sizes<<<cdiv(ns, 256), 256, 0, s>>>(p->sl_len, ns, p->sl_ptr);
+    DDG_LAUNCH_CHECK();
+    DDG_CU(cudaMemsetAsync(p->sl_ptr + ns, 0, sizeof(int), s));
+    int total = 0;
+    DDG_TRY(scan_exclusive(c, p->sl_ptr, p->sl_ptr, ns + 1, &total, s));
+    DDG_TRY(dalloc(c, p->a_matrix, &p->sl_col, std::max(total, 1)));
+    DDG_TRY(dalloc(c, p->a_matrix, &p->sl_val, std::max(total, 1)));
+    k_sell_fill<<<cdiv(n, 256), 256, 0, s>>>(p->rowptr, p->col, p->val, p->sl_perm, p->sl_len, p->sl_ptr, n,
+                                            p->sl_col, p->sl_val);
+    DDG_LAUNCH_CHECK();
+    DDG_LAUNCHES(3);
+    return DDG_OK;
+}
+
+// y_row = sum_e val_e x[col_e] for the row of slot k: the first eight entries' columns and values
+// are loaded under predicates, then their x gathers, so that all of them are in flight at once
+__device__ __forceinline__ double sell_row(const int *__restrict__ scol, const double *__restrict__ sval,
+                                           const int *__restrict__ slen, const int *__restrict__ sptr,
+                                           const double *__restrict__ x, int k) {
+    const int L = slen[k / SL_W];
+    const int *cp = scol + sptr[k / SL_W] + (k % SL_W);
+    const double *vp = sval + sptr[k / SL_W] + (k % SL_W);
+    int c[8];
+    double v[8], xv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        c[e] = e < L ? cp[SL_W * e] : 0;
+        v[e] = e < L ? vp[SL_W * e] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) xv[e] = e < L ? x[c[e]] : 0.0;
     double acc = 0.0;
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += val[e] * x[col[e]];
-    y[i] = acc;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        if (e < L) acc += v[e] * xv[e];
+    for (int e = 8; e < L; ++e) acc += vp[SL_W * e] * x[cp[SL_W * e]];
+    return acc;
+}
+
+__global__ void __launch_bounds__(KT) k_spmv(const int *__restrict__ scol, const double *__restrict__ sval,
+                                             const int *__restrict__ slen, const int *__restrict__ sptr,
+                                             const int *__restrict__ perm, const double *__restrict__ x,
+                                             double *__restrict__ y, int n) {
+    const int k = blockIdx.x * KT + threadIdx.x;
+    if (k >= n) return;
+    y[perm[k]] = sell_row(scol, sval, slen, sptr, x, k);
 }
 
 int32_t spmv(ddg_problem *p, const double *x, double *y, cudaStream_t s) {
-    k_spmv<<<cdiv(p->nf, KT), KT, 0, s>>>(p->rowptr, p->col, p->val, x, y, p->nf);
+    k_spmv<<<cdiv(p->nf, KT), KT, 0, s>>>(p->sl_col, p->sl_val, p->sl_len, p->sl_ptr, p->sl_perm, x, y, p->nf);
     DDG_LAUNCH_CHECK();
     return DDG_OK;
 }
@@ -387,25 +478,21 @@ __global__ void __launch_bounds__(KT, 4) k_pupdate(const double *z, double *P, l
     }
 }
 
-// q = A p with the partial dots p.q and p.r, rows strided over the grid (up to eight CTAs per SM,
-// a few rows per thread); the first eight entries of a row are loaded under predicates, so that
-// their loads are all in flight at once, the rest in a loop; the last block forms
+// q = A p with the partial dots p.q and p.r, slots of the sliced ELLPACK matrix strided over
+// the grid (up to eight CTAs per SM, a few rows per thread); the last block forms
 // alpha = (p.r) / (p.q)
-__global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                 const double *__restrict__ val, const double *__restrict__ p,
+__global__ void __launch_bounds__(KT) k_spmv_fcg(const int *__restrict__ scol, const double *__restrict__ sval,
+                                                 const int *__restrict__ slen, const int *__restrict__ sptr,
+                                                 const int *__restrict__ perm, const double *__restrict__ p,
                                                  double *__restrict__ q, int n, const double *__restrict__ r,
                                                  double *part, Window win, double *scal, int *flag) {
     __shared__ double sh[2 * KT];
     __shared__ double tot[2];
     if (flag[F_STOP]) return;
     double d[2] = {0.0, 0.0};  // p.q, p.r
-    for (long long i = (long long)blockIdx.x * KT + threadIdx.x; i < n; i += (long long)gridDim.x * KT) {
-        const int e0 = rowptr[i], len = rowptr[i + 1] - e0;
-        double acc = 0.0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-            if (e < len) acc += val[e0 + e] * p[col[e0 + e]];
-        for (int e = 8; e < len; ++e) acc += val[e0 + e] * p[col[e0 + e]];
+    for (int k = blockIdx.x * KT + threadIdx.x; k < n; k += gridDim.x * KT) {
+        const double acc = sell_row(scol, sval, slen, sptr, p, k);
+        const int i = perm[k];
         q[i] = acc;
         const double pi = p[i];
         d[0] += pi * acc;
@@ -695,7 +782,8 @@ struct FcgRun {
             DDG_LAUNCHES(1);
         }
         k_pupdate<<<PUG, KT, 0, s>>>(z, P, ld, win, nf, scal, flag);
-        k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->rowptr, p->col, p->val, pn, qn, nf, r, part + off_sp, win, scal, flag);
+        k_spmv_fcg<<<nb_spmv, KT, 0, s>>>(p->sl_col, p->sl_val, p->sl_len, p->sl_ptr, p->sl_perm, pn, qn, nf, r,
+                                          part + off_sp, win, scal, flag);
         k_xr<<<G, KT, 0, s>>>(x, r, pn, qn, nf, scal, part + off_rr, flag, rtol, p->khist, p->khist_cap);
         nl += 3;
         DDG_LAUNCHES(3);

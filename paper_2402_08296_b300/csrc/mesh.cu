@@ -352,6 +352,7 @@ int32_t assemble(ddg_problem *p, const double *r9, const double *f_nodal_host, c
                                              p->dir, p->free_id, p->free_node, p->g, nf, q, fn, p->rowptr,
                                              p->col, p->val, p->b);
     DDG_LAUNCH_CHECK();
+    DDG_TRY(sell_build(p));
     DDG_CU(cudaStreamSynchronize(s));
     p->assembled = true;
     return check_status(p, "assemble");
