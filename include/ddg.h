@@ -258,7 +258,9 @@ int32_t ddg_apply_A(ddg_problem *p, const double *x_dev, double *y_dev, ddg_stre
  * Scratch is a 512 KiB array compiled into the library, which every GPU that
  * loads the library holds until the process exits; n_free may be at most
  * 16,777,216 (DDG_TOO_LARGE beyond).  The first call on a device looks up the
- * array's device address, so make that first call before any stream capture.
+ * array's device address, so make that first call before any stream capture;
+ * the address is kept for the life of the process, so do not use this call
+ * after a device reset in the same process.
  * All calls share the array: calls that overlap on the GPU race and their dot
  * products are then wrong; order them on one stream.  Errors:
  * DDG_INVALID_ARG, DDG_TOO_LARGE, DDG_CUDA_ERROR. */
