@@ -300,25 +300,37 @@ def run_ours(a, rank, world, local_rank):
     eb.record(cur)
     torch.cuda.synchronize()
     standalone_ms = ea.elapsed_time(eb) / n_app
-    # the fine SpMV on its own (HBM-bound): y = A x on the library's stream, one launch at a time
-    # with L2 flushed (a 512 MB write on the same stream) before each, so that the matrix
-    # (about 104 MB at 1M rows, less than the 126 MB L2) comes from HBM every time
+    # the fine SpMV on its own (HBM-bound): y = A x on the library's stream, one launch at a time.
+    # Before each launch L2 is flushed by a 512 MB write and then a 512 MB read of another buffer:
+    # none of the SpMV's inputs (about 104 MB at 1M rows, less than the 126 MB L2) stays cached,
+    # and no dirty line of the flush is left for the SpMV to write back (a write-only flush leaves
+    # about 120 MB of them, whose write-back would be timed with the SpMV; reported beside it)
     n_f = info["n_free"]
     xs_dev = torch.as_tensor(synth.residual_vector(n_f, 8)).cuda()
     ys_dev = torch.zeros_like(xs_dev)
+    clean = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
     for _ in range(3):
         ddg.ddg_apply_A(p, xs_dev, ys_dev, stream=stream)
     torch.cuda.synchronize()
     n_spmv = 20
-    spmv_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_spmv)]
-    with torch.cuda.stream(stream):
-        for sa, sb in spmv_ev:
-            flush.fill_(1.0)
-            sa.record(stream)
-            ddg.ddg_apply_A(p, xs_dev, ys_dev, stream=stream)
-            sb.record(stream)
-    torch.cuda.synchronize()
-    spmv_ms = float(np.mean([sa.elapsed_time(sb) for sa, sb in spmv_ev]))
+
+    def time_spmv(read_flush):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_spmv)]
+        with torch.cuda.stream(stream):
+            for sa, sb in evs:
+                flush.fill_(1.0)
+                if read_flush:
+                    sink.add_(clean.sum())
+                sa.record(stream)
+                ddg.ddg_apply_A(p, xs_dev, ys_dev, stream=stream)
+                sb.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([sa.elapsed_time(sb) for sa, sb in evs]))
+
+    spmv_ms = time_spmv(True)
+    spmv_ms_write_flush = time_spmv(False)
+    del clean
     nnz = int(ddg.ddg_matrix_download(p)[0][-1])
     spmv_bytes = 12 * nnz + 4 * (n_f + 1) + 8 * n_f + 8 * n_f   # values+columns, row pointers, y, x once
     # the roofline uses the CUDA events recorded around the GNN's launches inside the timed solves
@@ -395,7 +407,11 @@ def run_ours(a, rank, world, local_rank):
                               "unit": "GB/s", "frac": spmv_bytes / (spmv_ms / 1e3) / 1e9 / hbm_peak,
                               "peak_source": hbm_src, "bytes_per_launch": spmv_bytes, "nnz": nnz,
                               "avg_launch_ms": spmv_ms,
-                              "timing": f"CUDA events on the library stream around each of {n_spmv} launches, L2 flushed before each"}},
+                              "timing": f"CUDA events on the library stream around each of {n_spmv} launches; before "
+                                        "each, a 512 MB write and a 512 MB read of another buffer (L2 holds none "
+                                        "of the inputs and no dirty lines)",
+                              "avg_launch_ms_write_flush_only": spmv_ms_write_flush,
+                              "frac_write_flush_only": spmv_bytes / (spmv_ms_write_flush / 1e3) / 1e9 / hbm_peak}},
         "clocks": clk,
     }
     return out

@@ -866,6 +866,23 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     float2 *XY = reinterpret_cast<float2 *>(HS + (size_t)own * 3);    // [nn]
     const f2_t *Wp = reinterpret_cast<const f2_t *>(W.w);
     const float4 *hrow_in = reinterpret_cast<const float4 *>(h_in);  // rows of 12: h[10], c, 0
+    // the plan data of this thread's own nodes and of phase A's first needed node: set-up data,
+    // loaded before waiting for the previous block
+    int4 pinf[2];
+    int pe0[2], pe1[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int u = p * T + tid;
+        pinf[p] = make_int4(0, -1, 0, 0);
+        pe0[p] = pe1[p] = 0;
+        if (u < own) {
+            pinf[p] = INFO[u];
+            pe0[p] = APTR[u];
+            pe1[p] = APTR[u + 1];
+        }
+    }
+    const int node0 = tid < nn ? need[tid] : 0;
+    const float2 xy0 = tid < nn ? a.loc_xy[node0] : make_float2(0.f, 0.f);
     // launched as a programmatic dependent of the previous block: everything above reads
     // set-up data only; wait here until the previous launch's latents are complete and visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -878,9 +895,8 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
 #pragma unroll
         for (int o = 0; o < D; ++o) h[o] = 0.f;
         if (tid < nn) {
-            const int node = need[tid];
-            xy = a.loc_xy[node];
-            if (!first) load_hrow(hrow_in, node, h, cl);
+            xy = xy0;
+            if (!first) load_hrow(hrow_in, node0, h, cl);
         }
         for (int u = tid; u < nn; u += T) {
             float hn[D], cn = 0.f;
@@ -910,7 +926,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
     for (int p = 0; p < 2; ++p) {
         const int u = p * T + tid;
         if (u >= own) continue;
-        const int4 inf = INFO[u];
+        const int4 inf = pinf[p];
         const int node = inf.x;
         const bool inner = inf.y >= 0;
         float hp[D], c;  // from the copy phase A left in shared memory
@@ -923,7 +939,7 @@ __device__ __forceinline__ void fused_chunk(const FusedWeights &W, const ChunkAr
             load_hrow(HS, u, hp, c);
         }
         const float2 xj = XY[u];
-        const int e0 = APTR[u], e1 = APTR[u + 1];
+        const int e0 = pe0[p], e1 = pe1[p];
         f2_t so[D / 2], si[D / 2], pao[D / 2], pai[D / 2];
         const int n_out = min((int)((unsigned)inf.w >> 24), e1 - e0);  // out-messages (neighbours that are unknowns)
         const float dout = (float)n_out;
