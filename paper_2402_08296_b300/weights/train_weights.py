@@ -10,7 +10,7 @@ learning rate drops x0.1 when the mean loss of a pass over all meshes stops
 improving.
 
 Usage (needs a GPU): python paper_2402_08296_b300/weights/train_weights.py --minutes 15 [--kbar 30]
-    [--init weights.npy --lr 1e-3]
+    [--init weights.npy --lr 1e-3] [--nodes 50000 --nodes-max 200000] [--patience 4]
 Writes dss_k{kbar}_d10.npy (flat float32 weights, layout of include/ddg.h): of the weights after
 every pass, those with which DDM-GNN FCG needs the fewest iterations on a held-out domain.
 """
@@ -37,6 +37,10 @@ def main():
     ap.add_argument("--minutes", type=float, default=15.0)
     ap.add_argument("--meshes", type=int, default=8)
     ap.add_argument("--nodes", type=int, default=30000)
+    ap.add_argument("--nodes-max", type=int, default=0,
+                    help="if given, mesh sizes log-uniform between --nodes and this (seeded)")
+    ap.add_argument("--patience", type=int, default=2,
+                    help="passes without a 1 %% lower mean loss before the learning rate drops x0.1")
     ap.add_argument("--steps", type=int, default=200, help="optimiser steps per mesh and pass")
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--harvest", type=int, default=60)
@@ -67,9 +71,13 @@ def main():
         rep, _ = ddg.ddg_fcg_solve(val, 1e-6, 1000, 10, want_x=False)
         return rep["iterations"] if rep["status"] == ddg.DDG_OK else 10 ** 6
     problems = []
+    sizes = [a.nodes] * a.meshes
+    if a.nodes_max > a.nodes:
+        rng = np.random.default_rng(4999)
+        sizes = [int(round(np.exp(rng.uniform(np.log(a.nodes), np.log(a.nodes_max))))) for _ in range(a.meshes)]
     for s in range(a.meshes):
         seed = 5000 + s
-        m = synth.star_mesh(a.nodes, seed=seed)
+        m = synth.star_mesh(sizes[s], seed=seed)
         K = max(1, int(round((m.n - m.n_boundary_ring) / 1000.0)))
         p = ddg.ddg_mesh_upload(ctx, m.xy, m.tri)
         ddg.ddg_assemble_poly(p, synth.poly_coeffs(seed))
@@ -101,7 +109,7 @@ def main():
             best, stale = mean, 0
         else:
             stale += 1
-            if stale >= 2:
+            if stale >= a.patience:
                 lr, stale = lr * 0.1, 0
         rnd += 1
     np.save(a.out, best_w)
