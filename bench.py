@@ -44,10 +44,10 @@ GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused", 
 # DRAM bytes (read + write) per GNN application from an ncu capture of the current kernel form,
 # keyed by (workload, schedule, chunk width); absent (null in the line) when no capture of the
 # current kernel exists for the workload.  From profiles/k_dss_fused_star1m.md: first block
-# 152.6 MB, each of the 28 middle blocks 222.3 MB, last block 185.6 MB.
-GNN_TRAFFIC: dict = {("star1m", 3, 256): int(152.6e6 + 28 * 222.3e6 + 185.6e6)}
+# 152.3 MB, each of the 28 middle blocks 221.6 MB, last block 188.5 MB.
+GNN_TRAFFIC: dict = {("star1m", 3, 256): int(152.3e6 + 28 * 221.6e6 + 188.5e6)}
 # FCG iterations of the GPU path with the committed weights (the reference arm's scale)
-GNN_ITERATIONS = {"star1m": 76, "star100k": 71}
+GNN_ITERATIONS = {"star1m": 76, "star100k": 70}
 
 
 def args_parse():
@@ -70,7 +70,7 @@ def args_parse():
                     help="also measure the FP32/FP64 FMA rates with the library's probe (roofline context)")
     ap.add_argument("--ref-iterations", type=int, default=0,
                     help="reference arm: FCG iterations a DDM-GNN oracle solve is scaled to (0: the GPU "
-                         "path's count with the committed weights for the workload, 76 on star1m, 71 on star100k)")
+                         "path's count with the committed weights for the workload, 76 on star1m, 70 on star100k)")
     ap.add_argument("--requests", type=int, default=24, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=50.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--n-min", type=int, default=10_000, help="serve workload: smallest mesh (nodes)")
@@ -313,10 +313,12 @@ def run_ours(a, rank, world, local_rank):
     for _ in range(3):
         ddg.ddg_apply_A(p, xs_dev, ys_dev, stream=stream)
     torch.cuda.synchronize()
-    n_spmv = 20
+    n_spmv, n_spmv_warm = 20, 3
 
     def time_spmv(read_flush):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_spmv)]
+        # n_spmv_warm untimed launches of the same flush-and-launch pattern first, then the median
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_spmv_warm + n_spmv)]
         with torch.cuda.stream(stream):
             for sa, sb in evs:
                 flush.fill_(1.0)
@@ -326,7 +328,7 @@ def run_ours(a, rank, world, local_rank):
                 ddg.ddg_apply_A(p, xs_dev, ys_dev, stream=stream)
                 sb.record(stream)
         torch.cuda.synchronize()
-        return float(np.mean([sa.elapsed_time(sb) for sa, sb in evs]))
+        return float(np.median([sa.elapsed_time(sb) for sa, sb in evs[n_spmv_warm:]]))
 
     spmv_ms = time_spmv(True)
     spmv_ms_write_flush = time_spmv(False)
@@ -407,9 +409,9 @@ def run_ours(a, rank, world, local_rank):
                               "unit": "GB/s", "frac": spmv_bytes / (spmv_ms / 1e3) / 1e9 / hbm_peak,
                               "peak_source": hbm_src, "bytes_per_launch": spmv_bytes, "nnz": nnz,
                               "avg_launch_ms": spmv_ms,
-                              "timing": f"CUDA events on the library stream around each of {n_spmv} launches; before "
-                                        "each, a 512 MB write and a 512 MB read of another buffer (L2 holds none "
-                                        "of the inputs and no dirty lines)",
+                              "timing": f"median of CUDA events on the library stream around each of {n_spmv} launches "
+                                        f"(after {n_spmv_warm} untimed); before each, a 512 MB write and a 512 MB "
+                                        "read of another buffer (L2 holds none of the inputs and no dirty lines)",
                               "avg_launch_ms_write_flush_only": spmv_ms_write_flush,
                               "frac_write_flush_only": spmv_bytes / (spmv_ms_write_flush / 1e3) / 1e9 / hbm_peak}},
         "clocks": clk,
