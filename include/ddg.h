@@ -81,8 +81,12 @@ typedef struct ddg_solve_report {
     int32_t launches;          /* all kernel launches of the library inside the loop */
     int32_t local_applies;     /* local-solve applications (one per iteration) */
     int32_t gnn_schedule;      /* 0: one launch per application, 1: one launch per message-passing block,
-                                  2: as 1 with the graphs cut into chunks of at most 2 * gnn_chunk_t nodes */
-    int32_t gnn_chunk_t;       /* threads per CTA of schedule 2 (0 otherwise) */
+                                  2: as 1 with the graphs cut into chunks of at most 2 * gnn_chunk_t nodes,
+                                  3: equal-work ranges of the concatenated graphs, packed FP32 (the default
+                                  pick), 4: as 3 with the per-node products on the tensor cores through
+                                  tensor memory, 5: any latent size d in {5, 10, 20}, 6: as 4 with
+                                  warp-synchronous tensor-core MMAs; -1 for DDM-LU */
+    int32_t gnn_chunk_t;       /* threads per CTA of the chunked schedules 2-6 (0 otherwise) */
 } ddg_solve_report;
 
 /* ---- context --------------------------------------------------------- */
