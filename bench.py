@@ -47,7 +47,7 @@ GNN_KERNELS = {0: "k_dss", 1: "k_dss_step", 2: "k_dss_chunk", 3: "k_dss_fused", 
 # 152.3 MB, each of the 28 middle blocks 221.6 MB, last block 188.5 MB.
 GNN_TRAFFIC: dict = {("star1m", 3, 256): int(152.3e6 + 28 * 221.6e6 + 188.5e6)}
 # FCG iterations of the GPU path with the committed weights (the reference arm's scale)
-GNN_ITERATIONS = {"star1m": 76, "star100k": 70}
+GNN_ITERATIONS = {"star1m": 75, "star100k": 70}
 
 
 def args_parse():
@@ -70,7 +70,7 @@ def args_parse():
                     help="also measure the FP32/FP64 FMA rates with the library's probe (roofline context)")
     ap.add_argument("--ref-iterations", type=int, default=0,
                     help="reference arm: FCG iterations a DDM-GNN oracle solve is scaled to (0: the GPU "
-                         "path's count with the committed weights for the workload, 76 on star1m, 70 on star100k)")
+                         "path's count with the committed weights for the workload, 75 on star1m, 70 on star100k)")
     ap.add_argument("--requests", type=int, default=24, help="serve workload: requests in the stream")
     ap.add_argument("--rate", type=float, default=50.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--n-min", type=int, default=10_000, help="serve workload: smallest mesh (nodes)")
