@@ -320,6 +320,9 @@ def run_ours(a, rank, world, local_rank):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(n_spmv_warm + n_spmv)]
         with torch.cuda.stream(stream):
+            # the GPU first spins for about 50 ms, so that the host has queued every flush, event and
+            # launch of the series before the GPU reaches them: no host latency inside an interval
+            torch.cuda._sleep(100_000_000)
             for sa, sb in evs:
                 flush.fill_(1.0)
                 if read_flush:
