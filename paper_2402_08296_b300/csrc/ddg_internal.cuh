@@ -333,7 +333,6 @@ int32_t dss_tc_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_hos
 // schedule 6 (dss_mma.cu): schedule 4's chunks, per-node products as warp-synchronous tensor-core MMAs
 constexpr int MMA_W_FLOATS = 3072;  // floats of one block's MMA weight fragments (four products)
 void mma_weight_image(const float *fused, int kbar, std::vector<float> &img);
-int32_t mma_ctas_per_sm(int *out);
 int32_t dss_mma_launch(ddg_problem *p, const ChunkArgs &a, const float *fused_host, const float *mma_w,
                        cudaStream_t s);
 // schedule 5 (dss_d.cu): latent sizes d = 5, 10, 20 from the flat weights, on schedule 2's chunks

@@ -465,8 +465,6 @@ static int32_t mma_configure(int *per_sm) {
     return DDG_OK;
 }
 
-int32_t mma_ctas_per_sm(int *out) { return mma_configure(out); }
-
 int32_t dss_mma_launch(ddg_problem *p, const ChunkArgs &base, const float *fused_host, const float *mma_w,
                        cudaStream_t s) {
     int per_sm = 0, sms = 0;
